@@ -1,0 +1,224 @@
+/*
+ * lagp.h -- C ABI of the GB300 (sm_103a) library for local approximate
+ * Gaussian process regression with ALC local design search
+ * (Gramacy, Niemi & Weiss, "Massively parallel approximate Gaussian process
+ * regression", arXiv:1310.5182).
+ *
+ * Notation follows the paper: X is the N x p design, Y the N responses, Xref
+ * the M reference (predictive) locations x; every location gets its own local
+ * design X_n(x) grown greedily from the n0 nearest neighbours to n rows, the
+ * search restricted to the N' nearest neighbours of x (Sec. 3.1).  The
+ * correlation is the isotropic Gaussian K(x,x') = exp(-||x - x'||^2 / d)
+ * (Sec. 2.1) with lengthscale d and nugget g: design matrices carry g on the
+ * diagonal, cross covariances carry none, and a candidate's self covariance
+ * is 1 + g.
+ *
+ * Conventions for every entry point below:
+ *  - Array arguments are DEVICE pointers owned by the caller (for example the
+ *    storage of PyTorch CUDA tensors), row-major and densely packed, except
+ *    in lagp_agp, whose arrays are HOST pointers.  The library never frees or
+ *    retains caller memory.
+ *  - Work is enqueued on the context's stream and is asynchronous with respect
+ *    to the host, except lagp_agp, which returns after its results are in host
+ *    memory.  The context owns a device workspace that grows on demand;
+ *    growing it synchronises the device.
+ *  - The return value reports argument and CUDA errors: LAGP_EINVAL for an
+ *    inconsistent size or parameter (nothing is launched), LAGP_ECUDA for a
+ *    failed CUDA call, LAGP_ENOMEM when the workspace cannot grow.  The text
+ *    of the last error is available from lagp_last_error().
+ *  - Numerical failures of single locations do not fail the call: the call
+ *    returns LAGP_OK, status[m] receives LAGP_ENOTPD (a local covariance
+ *    matrix that is not positive definite in floating point) and that
+ *    location's floating outputs are NaN (its index outputs -1).
+ *  - M = 0 is a no-op that returns LAGP_OK.
+ *  - A context must not be used from two host threads at once.
+ */
+#ifndef LAGP_H
+#define LAGP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LAGP_OK = 0,
+    LAGP_EINVAL = 1,   /* invalid argument: nothing was launched */
+    LAGP_ENOTPD = 2,   /* per-location: local matrix not positive definite */
+    LAGP_ECUDA = 3,    /* a CUDA runtime call failed */
+    LAGP_ETIMEOUT = 4, /* per-location: a bounded device-side wait gave up */
+    LAGP_ENOMEM = 5    /* workspace could not be allocated, or a bounded
+                          candidate buffer overflowed (lagp_knn) */
+} lagp_status;
+
+/* element type of X, Y and Xref */
+typedef enum { LAGP_F64 = 0, LAGP_F32 = 1 } lagp_dtype;
+
+/* arithmetic of the ALC search (lagp_alc_select)
+ *  LAGP_PREC_F64     the plain form: every candidate's criterion evaluated
+ *                    with Eq. (dxy) in FP64, O(j^2) per candidate per step.
+ *  LAGP_PREC_F32BULK candidates screened in FP32 through the Schur-complement
+ *                    form of the same criterion (O(j) per candidate per
+ *                    step); the leading contenders are re-scored with
+ *                    Eq. (dxy) in FP64, and the partitioned-inverse update of
+ *                    K_j^{-1} stays in FP64. */
+typedef enum { LAGP_PREC_F64 = 0, LAGP_PREC_F32BULK = 1 } lagp_precision;
+
+typedef struct lagp_ctx lagp_ctx;
+
+/* Tunables of the persistent kernels.  Zero fields mean "choose
+ * automatically" (a per-shape choice made by the built-in tuner). */
+typedef struct {
+    int32_t ctas_per_sm;    /* resident CTAs per SM of the ALC kernels */
+    int32_t block_threads;  /* threads per CTA of the ALC kernels */
+    int32_t rescore_max;    /* F32BULK: most candidates re-scored in FP64 per
+                               step, 1..32 (default 8) */
+    double rescore_rel;     /* F32BULK: a candidate is re-scored in FP64 when
+                               its FP32 score is within this relative margin
+                               of the FP32 maximum (default 0.05) */
+} lagp_tuning;
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle.  Returns LAGP_EINVAL for a bad device, LAGP_ECUDA on failure. */
+lagp_status lagp_create(lagp_ctx **ctx, int device, void *cuda_stream);
+
+/* Release the context and its workspace (synchronises its stream).  NULL is
+ * accepted. */
+lagp_status lagp_destroy(lagp_ctx *ctx);
+
+/* Switch the stream later calls enqueue on. */
+lagp_status lagp_set_stream(lagp_ctx *ctx, void *cuda_stream);
+
+/* Text of the last error on this context ("" if none); valid until the next
+ * call on the context. */
+const char *lagp_last_error(const lagp_ctx *ctx);
+
+/* Name of a status code. */
+const char *lagp_status_string(lagp_status s);
+
+lagp_status lagp_get_tuning(const lagp_ctx *ctx, lagp_tuning *out);
+lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in);
+
+/* Number of kernels this context has launched since creation (all entry
+ * points), for launch accounting. */
+int64_t lagp_launch_count(const lagp_ctx *ctx);
+
+/* ---------------------------------------------------------------- a1: kNN
+ * Exact N'-nearest-neighbour candidate sets (Sec. 3.1: the ALC search is
+ * restricted to the N' nearest neighbours of x; Fig. 1 step 2(a) takes the
+ * first n0 of them as the initial design).
+ *   X       N x p design (dtype)            Xref  M x p locations (dtype)
+ *   Nprime  M per-location N' values, or NULL (all = Nprime_max)
+ *   idx     M x Nprime_max int32 output: design rows sorted by ascending
+ *           (d2, row), where d2 = sum_i (x_i - X_{r,i})^2 is accumulated in
+ *           FP64 in coordinate order without fused multiply-add; entries past
+ *           Nprime[m] are -1.  The result is bit-exact and deterministic.
+ *   status  M int32 output or NULL: LAGP_OK; LAGP_EINVAL (Nprime[m] outside
+ *           [1, Nprime_max], or non-finite distances); LAGP_ENOMEM (more than
+ *           min(2 Nprime_max + 1024, 8192) design rows lie within FP32
+ *           screening resolution of the N'-th distance, i.e. massively
+ *           duplicated rows).  A failed location's idx row is -1.
+ * Requires 1 <= Nprime_max <= min(N, 4096), N < 2^31 and 1 <= p <= 64. */
+lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                     const void *Xref, int64_t M, const int32_t *Nprime, int32_t Nprime_max,
+                     int32_t *idx, int32_t *status);
+
+/* ---------------------------------------------- a2..a6: greedy ALC search
+ * Local designs by the greedy ALC search of Fig. 1 step 2: the first n0
+ * candidates of idx form X_{n0}(x); for j = n0..n[m]-1 the candidate that
+ * maximises the reduction in variance v_j(x) - v_{j+1}(x) of Eq. (dxy)
+ * (with g_j, m_j of Eq. (piedef)) joins the design and K_j^{-1} grows by the
+ * partitioned inverse (Sec. 2.2).  Exact ties go to the lower design row.
+ *   X, Xref     as lagp_knn;  idx, Nprime, Nprime_max  as produced by lagp_knn
+ *               (Nprime_max <= 4096); a location whose idx row holds a row
+ *               outside [0, N), or whose n[m] / Nprime[m] are inconsistent,
+ *               gets status LAGP_EINVAL
+ *   n0          initial nearest-neighbour design size, >= 1
+ *   n           M final design sizes (n0 <= n[m] <= Nprime[m]), or NULL
+ *               (all = n_max)
+ *   d           M lengthscales (> 0);  g  nugget (>= 0)
+ *   prec        LAGP_PREC_F64 or LAGP_PREC_F32BULK (see lagp_precision)
+ *   sel         M x n_max int32 output: the chosen design rows in the order
+ *               chosen (the n0 seeds first); -1 past n[m]
+ *   alc         M x n_max FP64 output or NULL: raw Delta of Eq. (dxy) of the
+ *               row chosen at step j (NaN for the seeds and past n[m]);
+ *               multiplying by psi_j / (j - 2) gives the normalised value of
+ *               the paper's step 9
+ *   status      M int32 output: LAGP_OK / LAGP_ENOTPD / LAGP_EINVAL per
+ *               location */
+lagp_status lagp_alc_select(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
+                            lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
+                            const int32_t *Nprime, int32_t Nprime_max, int32_t n0,
+                            const int32_t *n, int32_t n_max, const double *d, double g,
+                            lagp_precision prec, int32_t *sel, double *alc, int32_t *status);
+
+/* ------------------------------------------------------ a7: local predict
+ * Predictive equations (Eqs. predgp, preds2) on each location's local design:
+ *   mean = k^T K^{-1} Y_n,   psi = Y_n^T K^{-1} Y_n,
+ *   s2   = psi (1 + g - k^T K^{-1} k) / n,   df = n,
+ * with K_n factorised by FP64 Cholesky.  The predictive variance is
+ * s2 * df / (df - 2).
+ *   Y      N responses (dtype);  sel  M x n_max design rows (from
+ *          lagp_alc_select);  n  M sizes or NULL (= n_max);  d  M lengthscales
+ *          (a location whose sel row holds a row outside [0, N), n[m] outside
+ *          [1, n_max] or d[m] <= 0 gets status LAGP_EINVAL, NaN outputs)
+ *   mean, s2, df   M FP64 outputs;  status  M int32 outputs */
+lagp_status lagp_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                         lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *sel,
+                         const int32_t *n, int32_t n_max, const double *d, double g,
+                         double *mean, double *s2, double *df, int32_t *status);
+
+/* ------------------------------------------------------- a8: local MLE
+ * Per-location Newton maximisation in d of the concentrated log-likelihood
+ * of Eq. (gpk), log p(Y_n | d) = log Gamma(n/2) - (n/2) log(2 pi)
+ *   - (1/2) log|K_n| - (n/2) log(psi/2), on the local design (Fig. 1 step 3),
+ * with analytic first and second derivatives in d, all in FP64.  Step rule:
+ * Newton step -l'/l'' when l'' < 0, else doubling/halving in the gradient's
+ * direction; proposals are clipped to [dmin, dmax] and halved (at most 20
+ * times) until l does not decrease; stop when the step is below 1e-10 d,
+ * when no halving recovers an increase, or after max_iter iterations.
+ *   d       M lengthscales, in: starting values, out: estimates
+ *   llik, dllik, d2llik   M FP64 outputs at the final d (any may be NULL)
+ *   iters   M int32 iterations taken (may be NULL);  status  M int32
+ * max_iter = 0 evaluates the likelihood and its derivatives at d only. */
+lagp_status lagp_mle_step(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                          lagp_dtype dtype, int64_t M, const int32_t *sel, const int32_t *n,
+                          int32_t n_max, double *d, double g, double dmin, double dmax,
+                          int32_t max_iter, double *llik, double *dllik, double *d2llik,
+                          int32_t *iters, int32_t *status);
+
+/* ------------------------------------------- adjoint of a7 / a8 in (d, g)
+ * Analytic derivatives of the local predictive mean and scale (Eqs. predgp,
+ * preds2) and of the log-likelihood (Eq. gpk) with respect to the
+ * lengthscale d and the nugget g, per location, FP64:
+ *   dK/dd = (D/d^2) o exp(-D/d),   dK/dg = I,   d(K^{-1}) = -K^{-1} dK K^{-1}.
+ * Outputs are M-vectors (any may be NULL except status). */
+lagp_status lagp_predict_grad(lagp_ctx *ctx, const void *X, const void *Y, int64_t N,
+                              int32_t p, lagp_dtype dtype, const void *Xref, int64_t M,
+                              const int32_t *sel, const int32_t *n, int32_t n_max,
+                              const double *d, double g, double *dmean_dd, double *dmean_dg,
+                              double *ds2_dd, double *ds2_dg, double *dllik_dd,
+                              double *dllik_dg, int32_t *status);
+
+/* --------------------------------------------- whole method, host buffers
+ * The multi-stage algorithm of Fig. 1 for every reference location:
+ * kNN (a1) -> greedy ALC design at lengthscale d0 (a2..a6) -> optional local
+ * MLE of d on that design (a8, when do_mle != 0) -> prediction (a7) with the
+ * final d.  All array arguments are HOST pointers; the inputs are copied to
+ * the device, and the outputs copied back, inside the call, which returns
+ * after the outputs are in host memory.
+ *   Nprime, n   M per-location values or NULL (all = Nprime_max / n_max)
+ *   mean, s2, df, status   M outputs;  d_out  M final lengthscales or NULL */
+lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                     lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *Nprime,
+                     int32_t Nprime_max, int32_t n0, const int32_t *n, int32_t n_max,
+                     double d0, double g, lagp_precision prec, int32_t do_mle, double dmin,
+                     double dmax, int32_t max_iter, double *mean, double *s2, double *df,
+                     double *d_out, int32_t *status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAGP_H */

@@ -1,0 +1,290 @@
+// a2..a6, plain FP64 form: greedy ALC local design search (Fig. 1 step 2 of
+// the paper) with every candidate's criterion evaluated by Eq. (dxy) in FP64.
+//
+// Layout: one persistent CTA works on one location at a time (locations are
+// taken from an atomic counter).  Shared memory holds K_j^{-1} (FP64, leading
+// dimension n_max) and the design's k_j(x); a per-CTA global panel holds
+// K(x_c, x_i) for every candidate c and design row i, one column appended per
+// step (the paper rebuilds these covariances every step; appending gives the
+// same values for N' exponentials per step instead of N' j).
+//
+// Per step j, one warp per candidate (lane t owns design index t, t+32, ...):
+//   b   = K_j^{-1} k_j(x_c)                 (the O(j^2) contraction, paper step 3)
+//   m^-1 = 1 + g - k_j(x_c)^T b,  k_j(x)^T g_j = -m k_j(x)^T b   (steps 4-5, 7)
+//   Delta = (k^T g)^2 m^-1 + 2 (k^T g) K(x_c,x) + K(x_c,x)^2 m      (Eq. dxy, step 8)
+// then a block argmax (ties to the lower design row) and the partitioned
+// inverse update of Sec. 2.2.  GB300 runs FP64 at 1/62 of the FP32 rate, so
+// this form is bound by the FP64 pipe; it is the plain reference form.
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "lagp_internal.h"
+
+namespace {
+
+constexpr int F64_THREADS = 256;
+constexpr int F64_WARPS = F64_THREADS / 32;
+constexpr int NMAX_SMEM = 128;
+
+struct F64Shared {
+    double *Kinv;    // nmax x nmax
+    double *kx;      // nmax: k_j(x)
+    double *bstar;   // nmax: K^{-1} k*
+    double *xd;      // nmax x p: design coordinates
+    double *xq;      // p: reference location
+    unsigned char *chosen;  // Npmax
+};
+
+// Contraction for one candidate (paper steps 3-4 and the k_j(x) dot product
+// of step 7): lane t accumulates b_t = sum_k K^{-1}[k][t] kc[k] for its
+// columns t = lane + 32 r, r < JQ; returns warp-uniform kc^T b and kx^T b.
+// K^{-1} rows have leading dimension ld (a multiple of 32), so every read is
+// inside the row; columns >= j are masked out of the sums.
+template <int JQ>
+__device__ __forceinline__ void contract_cand(const double *__restrict__ prow, const double *Kinv,
+                                              int ld, const double *kx, int j, int lane,
+                                              double &quad, double &kxb) {
+    double kc[JQ], b[JQ];
+#pragma unroll
+    for (int r = 0; r < JQ; r++) {
+        kc[r] = (lane + 32 * r < j) ? prow[lane + 32 * r] : 0.0;
+        b[r] = 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < JQ; r++) {
+        const int kend = min(32, j - 32 * r);
+        for (int kk = 0; kk < kend; kk++) {
+            const double v = __shfl_sync(LAGP_FULL_MASK, kc[r], kk);
+            const double *row = Kinv + (size_t)(32 * r + kk) * ld + lane;
+#pragma unroll
+            for (int r2 = 0; r2 < JQ; r2++) b[r2] = fma(row[32 * r2], v, b[r2]);
+        }
+    }
+    double q = 0.0, x = 0.0;
+#pragma unroll
+    for (int r = 0; r < JQ; r++)
+        if (lane + 32 * r < j) {
+            q = fma(kc[r], b[r], q);
+            x = fma(kx[lane + 32 * r], b[r], x);
+        }
+    quad = warp_sum(q);
+    kxb = warp_sum(x);
+}
+
+__device__ __forceinline__ double kern64(const double *a, const void *X, int64_t r, int p,
+                                         lagp_dtype dt, double d) {
+    double s = 0.0;
+    for (int i = 0; i < p; i++) {
+        double diff = a[i] - load_coord64(X, r, p, i, dt);
+        s += diff * diff;
+    }
+    return exp(-s / d);
+}
+
+__global__ void __launch_bounds__(F64_THREADS)
+alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_ws,
+               double *__restrict__ kappa_ws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = a.nmax, p = a.p, Npmax = a.Npmax;
+    const int ld = (nmax + 31) & ~31;  // K^{-1} leading dimension
+    F64Shared S;
+    S.Kinv = reinterpret_cast<double *>(smem_raw);
+    S.kx = S.Kinv + (size_t)(nmax + 1) * ld;
+    S.bstar = S.kx + ld;
+    S.xd = S.bstar + nmax;
+    S.xq = S.xd + (size_t)nmax * p;
+    S.chosen = reinterpret_cast<unsigned char *>(S.xq + p);
+    __shared__ int s_loc, s_bad, s_cstar;
+    __shared__ double w_v[F64_WARPS];
+    __shared__ int w_row[F64_WARPS], w_slot[F64_WARPS];
+    __shared__ double s_delta, s_mu;
+
+    double *panel = panel_ws + (size_t)blockIdx.x * Npmax * nmax;  // [c][i], ld nmax
+    double *kappa = kappa_ws + (size_t)blockIdx.x * Npmax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (;;) {
+        if (tid == 0) s_loc = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t loc = s_loc;
+        __syncthreads();
+        if (loc >= a.M) break;
+
+        const int k = a.Np ? a.Np[loc] : Npmax;
+        const int nm = a.n ? a.n[loc] : nmax;
+        const double d = a.d[loc], g = a.g;
+        const int32_t *cands = a.idx + loc * Npmax;
+        int32_t *sel = a.sel + loc * nmax;
+        double *alc = a.alc ? a.alc + loc * nmax : nullptr;
+
+        // per-location validation
+        if (tid == 0) s_bad = (k < 1 || k > Npmax || nm < a.n0 || nm > nmax || nm > k || !(d > 0.0) ||
+                               !isfinite(d)) ? LAGP_EINVAL : LAGP_OK;
+        __syncthreads();
+        if (s_bad == LAGP_OK)
+            for (int c = tid; c < k; c += F64_THREADS) {
+                int32_t r = cands[c];
+                if (r < 0 || r >= a.N) s_bad = LAGP_EINVAL;
+            }
+        __syncthreads();
+        for (int t = tid; t < nmax; t += F64_THREADS) {
+            sel[t] = -1;
+            if (alc) alc[t] = CUDART_NAN;
+        }
+        if (s_bad != LAGP_OK) {
+            if (tid == 0) a.status[loc] = s_bad;
+            continue;  // next location (loop head synchronises)
+        }
+
+        // reference location, chosen flags, K(x_c, x) for every candidate
+        for (int i = tid; i < p; i += F64_THREADS) S.xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
+        for (int c = tid; c < k; c += F64_THREADS) S.chosen[c] = 0;
+        __syncthreads();
+        for (int c = tid; c < k; c += F64_THREADS) kappa[c] = kern64(S.xq, a.X, cands[c], p, a.dtype, d);
+        __syncthreads();
+
+        int status = LAGP_OK;
+        for (int j = 0; j < nm; j++) {
+            int cstar;
+            double delta = CUDART_NAN;
+            if (j < a.n0) {
+                cstar = j;  // Fig. 1 step 2(a): the nearest neighbours, in order
+            } else {
+                // ---- score every unchosen candidate, one warp per candidate
+                ArgBest best{0.0, -1, -1};
+                for (int c = warp; c < k; c += F64_WARPS) {
+                    if (S.chosen[c]) continue;
+                    const double *prow = panel + (size_t)c * nmax;
+                    double quad, kxb;
+                    switch ((j + 31) >> 5) {
+                        case 1: contract_cand<1>(prow, S.Kinv, ld, S.kx, j, lane, quad, kxb); break;
+                        case 2: contract_cand<2>(prow, S.Kinv, ld, S.kx, j, lane, quad, kxb); break;
+                        case 3: contract_cand<3>(prow, S.Kinv, ld, S.kx, j, lane, quad, kxb); break;
+                        default: contract_cand<4>(prow, S.Kinv, ld, S.kx, j, lane, quad, kxb); break;
+                    }
+                    const double minv = (1.0 + g) - quad;  // m_j^{-1}(x_c), Eq. (piedef)
+                    const double m = 1.0 / minv;
+                    const double kxg = -m * kxb;           // k_j(x)^T g_j(x_c)
+                    const double kap = kappa[c];
+                    double dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
+                    if (!(minv > 0.0)) dl = -CUDART_INF;  // breakdown, flagged below
+                    if (!(minv > 0.0) && lane == 0) s_bad = LAGP_ENOTPD;
+                    if (better(dl, cands[c], best.v, best.row)) best = ArgBest{dl, cands[c], c};
+                }
+                if (lane == 0) {
+                    w_v[warp] = best.v;
+                    w_row[warp] = best.row;
+                    w_slot[warp] = best.slot;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    ArgBest b0{w_v[0], w_row[0], w_slot[0]};
+                    for (int w = 1; w < F64_WARPS; w++)
+                        if (better(w_v[w], w_row[w], b0.v, b0.row)) b0 = ArgBest{w_v[w], w_row[w], w_slot[w]};
+                    s_cstar = b0.slot;
+                    s_delta = b0.v;
+                    if (b0.slot < 0) s_bad = LAGP_ENOTPD;
+                }
+                __syncthreads();
+                if (s_bad != LAGP_OK) {
+                    status = s_bad;
+                    break;
+                }
+                cstar = s_cstar;
+                delta = s_delta;
+            }
+            // ---- partitioned inverse update with x* = candidate cstar (Sec. 2.2)
+            const double *kst = panel + (size_t)cstar * nmax;
+            for (int t = tid; t < j; t += F64_THREADS) {
+                double s = 0.0;
+                for (int kk = 0; kk < j; kk++) s = fma(S.Kinv[(size_t)kk * ld + t], kst[kk], s);
+                S.bstar[t] = s;
+            }
+            __syncthreads();
+            if (tid < 32) {
+                double q = 0.0;
+                for (int t = lane; t < j; t += 32) q = fma(kst[t], S.bstar[t], q);
+                q = warp_sum(q);
+                if (lane == 0) {
+                    double minv = (1.0 + g) - q;
+                    s_mu = 1.0 / minv;
+                    if (!(minv > 0.0)) s_bad = LAGP_ENOTPD;
+                }
+            }
+            __syncthreads();
+            if (s_bad != LAGP_OK) {
+                status = s_bad;
+                break;
+            }
+            const double mu = s_mu;
+            // K^{-1} + g g^T / m with g = -mu b*:  += mu b* b*^T ; border = -mu b*
+            for (int e = tid; e < j * j; e += F64_THREADS) {
+                int r = e / j, c = e - r * j;
+                S.Kinv[(size_t)r * ld + c] = fma(mu * S.bstar[r], S.bstar[c], S.Kinv[(size_t)r * ld + c]);
+            }
+            for (int t = tid; t < j; t += F64_THREADS) {
+                double gt = -mu * S.bstar[t];
+                S.Kinv[(size_t)t * ld + j] = gt;
+                S.Kinv[(size_t)j * ld + t] = gt;
+            }
+            if (tid == 0) {
+                S.Kinv[(size_t)j * ld + j] = mu;
+                S.kx[j] = kappa[cstar];
+                S.chosen[cstar] = 1;
+                sel[j] = cands[cstar];
+                if (alc) alc[j] = delta;
+            }
+            for (int i = tid; i < p; i += F64_THREADS)
+                S.xd[(size_t)j * p + i] = load_coord64(a.X, cands[cstar], p, i, a.dtype);
+            __syncthreads();
+            // ---- append panel column j: K(x_c, x*) for every candidate (no nugget)
+            if (j + 1 < nm) {
+                const double *xs = S.xd + (size_t)j * p;
+                for (int c = tid; c < k; c += F64_THREADS)
+                    panel[(size_t)c * nmax + j] = kern64(xs, a.X, cands[c], p, a.dtype, d);
+            }
+            __syncthreads();
+        }
+        if (status != LAGP_OK) {
+            for (int t = tid; t < nmax; t += F64_THREADS) {
+                sel[t] = -1;
+                if (alc) alc[t] = CUDART_NAN;
+            }
+        }
+        if (tid == 0) a.status[loc] = status;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a) {
+    if (a.nmax > NMAX_SMEM)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: n_max above 128 is not supported");
+    cudaStream_t st = ctx->stream;
+    const size_t ld = (size_t)((a.nmax + 31) & ~31);
+    // K^{-1} (n_max x ld, plus one spare row so masked reads stay inside), kx, b*,
+    // design coordinates, reference location, chosen flags
+    size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 2 + (size_t)a.nmax * a.p * 8 +
+                  (size_t)a.p * 8 + (size_t)a.Npmax + 16;
+    if (smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory");
+    cudaFuncSetAttribute(alc_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f64_kernel, F64_THREADS, smem);
+    int per_sm = ctx->tuning.ctas_per_sm > 0 ? ctx->tuning.ctas_per_sm : 2;
+    if (occ > 0 && per_sm > occ) per_sm = occ;
+    int64_t grid = (int64_t)ctx->num_sms * per_sm;
+    if (grid > a.M) grid = a.M;
+    if (grid < 1) grid = 1;
+    char *ws = static_cast<char *>(lagp_ws(ctx, WS_ALC_PANEL,
+                                           (size_t)grid * a.Npmax * ((size_t)a.nmax + 1) * 8 + 256));
+    int *counter = static_cast<int *>(lagp_ws(ctx, WS_ALC_COUNTER, 256));
+    if (!ws || !counter) return LAGP_ENOMEM;
+    double *panel = reinterpret_cast<double *>(ws);
+    double *kappa = panel + (size_t)grid * a.Npmax * a.nmax;
+    LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
+    alc_f64_kernel<<<(unsigned)grid, F64_THREADS, smem, st>>>(a, counter, panel, kappa);
+    ctx->launches++;
+    LAGP_CUDA(ctx, cudaGetLastError());
+    return LAGP_OK;
+}

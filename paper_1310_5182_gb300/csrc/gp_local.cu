@@ -1,0 +1,613 @@
+// a7 (local prediction), a8 (local Newton MLE of d) and the analytic adjoint
+// of both in (d, g), on each location's selected design, all in FP64.
+//
+//   predict   Eqs. (predgp), (preds2): K_n = L L^T (Cholesky), z = L^{-1} Y_n,
+//             w = L^{-1} k_n(x);  mean = w^T z,  psi = z^T z,
+//             s2 = psi (1 + g - w^T w) / n,  df = n.
+//   MLE       Eq. (gpk): l(d) = log Gamma(n/2) - (n/2) log 2pi - (1/2) log|K|
+//             - (n/2) log(psi/2) with
+//             l'  = -1/2 tr(K^{-1}K') + (n/2) phi/psi,  phi = a^T K' a, a = K^{-1}Y,
+//             l'' = 1/2 tr(K^{-1}K'K^{-1}K') - 1/2 tr(K^{-1}K'')
+//                   + (n/2) [(a^T K'' a - 2 (K'a)^T K^{-1} (K'a))/psi + phi^2/psi^2],
+//             K' = (D/d^2) o E, K'' = (D^2/d^4 - 2D/d^3) o E, E = exp(-D/d);
+//             Newton steps with the safeguards stated in lagp.h.
+//   adjoint   d/dd and d/dg of mean and s2 through d(K^{-1}) = -K^{-1} dK K^{-1},
+//             and dl/dg = -1/2 tr(K^{-1}) + (n/2) a^T a / psi.
+// One CTA per location (persistent, atomic work counter); the n x n matrices
+// live in a per-CTA global workspace (L2-resident), vectors in shared memory.
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "lagp_internal.h"
+
+namespace {
+
+constexpr int GP_THREADS = 256;
+constexpr int GP_WARPS = GP_THREADS / 32;
+
+struct Blk {
+    int tid, lane, warp;
+};
+
+__device__ double block_sum(double v, double *red, const Blk &b) {
+    v = warp_sum(v);
+    __syncthreads();
+    if (b.lane == 0) red[b.warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < GP_WARPS; w++) s += red[w];
+    return s;
+}
+
+// Lower Cholesky of the symmetric n x n matrix A (lower triangle used) into L,
+// left-looking.  Returns false (block-uniform) if a pivot is not positive.
+__device__ bool block_cholesky(const double *A, double *L, int n, int ld, int *flag, const Blk &b) {
+    if (b.tid == 0) *flag = 1;
+    for (int c = 0; c < n; c++) {
+        if (b.warp == 0) {
+            double s = 0.0;
+            for (int k = b.lane; k < c; k += 32) s = fma(L[(size_t)c * ld + k], L[(size_t)c * ld + k], s);
+            s = warp_sum(s);
+            if (b.lane == 0) {
+                double piv = A[(size_t)c * ld + c] - s;
+                if (!(piv > 0.0)) *flag = 0;
+                L[(size_t)c * ld + c] = piv > 0.0 ? sqrt(piv) : 1.0;
+            }
+        }
+        __syncthreads();
+        const double lcc = L[(size_t)c * ld + c];
+        for (int i = c + 1 + b.tid; i < n; i += GP_THREADS) {
+            double s = A[(size_t)i * ld + c];
+            for (int k = 0; k < c; k++) s = fma(-L[(size_t)i * ld + k], L[(size_t)c * ld + k], s);
+            L[(size_t)i * ld + c] = s / lcc;
+        }
+        __syncthreads();
+    }
+    return *flag != 0;
+}
+
+// x = L^{-1} rhs by forward substitution, one warp.
+__device__ void warp_forward(const double *L, int ld, const double *rhs, double *x, int n, int lane) {
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int k = lane; k < i; k += 32) s = fma(L[(size_t)i * ld + k], x[k], s);
+        s = warp_sum(s);
+        if (lane == 0) x[i] = (rhs[i] - s) / L[(size_t)i * ld + i];
+        __syncwarp();
+    }
+}
+
+// x = L^{-T} rhs by backward substitution, one warp.
+__device__ void warp_backward(const double *L, int ld, const double *rhs, double *x, int n, int lane) {
+    for (int i = n - 1; i >= 0; i--) {
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < n; k += 32) s = fma(L[(size_t)k * ld + i], x[k], s);
+        s = warp_sum(s);
+        if (lane == 0) x[i] = (rhs[i] - s) / L[(size_t)i * ld + i];
+        __syncwarp();
+    }
+}
+
+struct GpWork {
+    double *D, *K, *L, *Li, *Ki, *A1;  // n x ld each
+};
+
+// Validate a location and load its design; returns the per-location status.
+__device__ int load_design(const GpArgs &a, int64_t loc, int nm, const double *dptr, double *xd,
+                           double *y, int *flag, const Blk &b) {
+    if (b.tid == 0) *flag = LAGP_OK;
+    __syncthreads();
+    const double d = dptr ? dptr[loc] : 1.0;
+    if (b.tid == 0 && (nm < 1 || nm > a.nmax || !(d > 0.0) || !isfinite(d))) *flag = LAGP_EINVAL;
+    __syncthreads();
+    if (*flag != LAGP_OK) return *flag;
+    const int32_t *s = a.sel + loc * a.nmax;
+    for (int t = b.tid; t < nm; t += GP_THREADS) {
+        int32_t r = s[t];
+        if (r < 0 || r >= a.N) *flag = LAGP_EINVAL;
+    }
+    __syncthreads();
+    if (*flag != LAGP_OK) return *flag;
+    for (int e = b.tid; e < nm * a.p; e += GP_THREADS) {
+        int t = e / a.p, i = e - t * a.p;
+        xd[e] = load_coord64(a.X, s[t], a.p, i, a.dtype);
+    }
+    for (int t = b.tid; t < nm; t += GP_THREADS)
+        y[t] = a.dtype == LAGP_F64 ? static_cast<const double *>(a.Y)[s[t]]
+                                   : (double)static_cast<const float *>(a.Y)[s[t]];
+    __syncthreads();
+    return LAGP_OK;
+}
+
+__device__ double sqd(const double *u, const double *v, int p) {
+    double s = 0.0;
+    for (int i = 0; i < p; i++) {
+        double df = u[i] - v[i];
+        s = fma(df, df, s);
+    }
+    return s;
+}
+
+// D (squared distances, lower triangle and diagonal) of the design.
+__device__ void build_D(const double *xd, int nm, int p, double *D, int ld, const Blk &b) {
+    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+        int i = e / nm, k = e - i * nm;
+        if (k <= i) {
+            double v = sqd(xd + (size_t)i * p, xd + (size_t)k * p, p);
+            D[(size_t)i * ld + k] = v;
+            D[(size_t)k * ld + i] = v;
+        }
+    }
+    __syncthreads();
+}
+
+// K = exp(-D/d) + g I (full symmetric).
+__device__ void build_K(const double *D, int nm, int ld, double d, double g, double *K, const Blk &b) {
+    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+        int i = e / nm, k = e - i * nm;
+        if (k <= i) {
+            double v = exp(-D[(size_t)i * ld + k] / d);
+            K[(size_t)i * ld + k] = v + (i == k ? g : 0.0);
+            K[(size_t)k * ld + i] = v + (i == k ? g : 0.0);
+        }
+    }
+    __syncthreads();
+}
+
+// log-likelihood of Eq. (gpk) at d: needs K built; leaves L and a = K^{-1} y.
+// Returns false if K is not positive definite.
+__device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, double *a, double *tmp,
+                           double *red, int *flag, double *out_l, double *out_psi, const Blk &b) {
+    if (!block_cholesky(W.K, W.L, nm, ld, flag, b)) return false;
+    if (b.warp == 0) {
+        warp_forward(W.L, ld, y, tmp, nm, b.lane);
+        warp_backward(W.L, ld, tmp, a, nm, b.lane);
+    }
+    __syncthreads();
+    double ld_part = 0.0, psi_part = 0.0;
+    for (int i = b.tid; i < nm; i += GP_THREADS) {
+        ld_part += 2.0 * log(W.L[(size_t)i * ld + i]);
+        psi_part += y[i] * a[i];
+    }
+    const double logdet = block_sum(ld_part, red, b);
+    const double psi = block_sum(psi_part, red, b);
+    const double hn = 0.5 * nm;
+    *out_l = lgamma(hn) - hn * log(2.0 * CUDART_PI) - 0.5 * logdet - hn * log(psi / 2.0);
+    *out_psi = psi;
+    return true;
+}
+
+// K^{-1} from L (needs L): Li = L^{-1}, Ki = Li^T Li.
+__device__ void inverse_from_L(const GpWork &W, int nm, int ld, const Blk &b) {
+    for (int c = b.warp; c < nm; c += GP_WARPS) {  // column c of L^{-1}
+        for (int i = 0; i < nm; i++) {
+            double val;
+            if (i < c) {
+                val = 0.0;
+            } else {
+                double s = 0.0;
+                for (int k = c + b.lane; k < i; k += 32) s = fma(W.L[(size_t)i * ld + k], W.Li[(size_t)k * ld + c], s);
+                s = warp_sum(s);
+                val = ((i == c ? 1.0 : 0.0) - s) / W.L[(size_t)i * ld + i];
+            }
+            if (b.lane == 0) W.Li[(size_t)i * ld + c] = val;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+        int i = e / nm, k = e - i * nm;
+        if (k <= i) {
+            double s = 0.0;
+            for (int r = i; r < nm; r++) s = fma(W.Li[(size_t)r * ld + i], W.Li[(size_t)r * ld + k], s);
+            W.Ki[(size_t)i * ld + k] = s;
+            W.Ki[(size_t)k * ld + i] = s;
+        }
+    }
+    __syncthreads();
+}
+
+struct Derivs {
+    double dl, d2l, dldg, trKi;
+};
+
+// First and second d-derivatives of l (and dl/dg); needs K, L, a, psi.
+__device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const double *a, double psi,
+                              double *t1, double *t2, double *red, const Blk &b) {
+    inverse_from_L(W, nm, ld, b);
+    const double d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
+    // K' into D's upper use: compute on the fly K'_ik = (D/d^2) E, E = K - g I
+    // A1 = K^{-1} K'
+    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+        int i = e / nm, k = e - i * nm;
+        double s = 0.0;
+        for (int r = 0; r < nm; r++) {
+            double Dr = W.D[(size_t)r * ld + k];
+            double Er = (r == k) ? 0.0 : W.K[(size_t)r * ld + k];
+            s = fma(W.Ki[(size_t)i * ld + r], (Dr / d2) * Er, s);
+        }
+        W.A1[(size_t)i * ld + k] = s;
+    }
+    // t1 = K' a
+    for (int i = b.tid; i < nm; i += GP_THREADS) {
+        double s = 0.0;
+        for (int k = 0; k < nm; k++) {
+            double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
+            s = fma((W.D[(size_t)i * ld + k] / d2) * E, a[k], s);
+        }
+        t1[i] = s;
+    }
+    __syncthreads();
+    double trA1 = 0.0, trA1A1 = 0.0, trKiK2 = 0.0, aK2a = 0.0, trKi = 0.0, ata = 0.0;
+    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+        int i = e / nm, k = e - i * nm;
+        trA1A1 = fma(W.A1[(size_t)i * ld + k], W.A1[(size_t)k * ld + i], trA1A1);
+        double Dik = W.D[(size_t)i * ld + k];
+        double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
+        double K2 = (Dik * Dik / d4 - 2.0 * Dik / d3) * E;
+        trKiK2 = fma(W.Ki[(size_t)i * ld + k], K2, trKiK2);
+        aK2a = fma(a[i] * K2, a[k], aK2a);
+        if (i == k) {
+            trA1 += W.A1[(size_t)i * ld + i];
+            trKi += W.Ki[(size_t)i * ld + i];
+            ata = fma(a[i], a[i], ata);
+        }
+    }
+    // t2 = K^{-1} t1
+    for (int i = b.tid; i < nm; i += GP_THREADS) {
+        double s = 0.0;
+        for (int k = 0; k < nm; k++) s = fma(W.Ki[(size_t)i * ld + k], t1[k], s);
+        t2[i] = s;
+    }
+    __syncthreads();
+    double phi_p = 0.0, chi_p = 0.0;
+    for (int i = b.tid; i < nm; i += GP_THREADS) {
+        phi_p = fma(a[i], t1[i], phi_p);
+        chi_p = fma(t1[i], t2[i], chi_p);
+    }
+    trA1 = block_sum(trA1, red, b);
+    trA1A1 = block_sum(trA1A1, red, b);
+    trKiK2 = block_sum(trKiK2, red, b);
+    aK2a = block_sum(aK2a, red, b);
+    trKi = block_sum(trKi, red, b);
+    ata = block_sum(ata, red, b);
+    const double phi = block_sum(phi_p, red, b);
+    const double chi = block_sum(chi_p, red, b);
+    const double hn = 0.5 * nm;
+    Derivs r;
+    r.dl = -0.5 * trA1 + hn * phi / psi;
+    r.d2l = 0.5 * trA1A1 - 0.5 * trKiK2 + hn * ((aK2a - 2.0 * chi) / psi + phi * phi / (psi * psi));
+    r.dldg = -0.5 * trKi + hn * ata / psi;
+    r.trKi = trKi;
+    return r;
+}
+
+struct GpShared {
+    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *xq;
+};
+
+__device__ GpShared carve(unsigned char *raw, int nmax, int p) {
+    GpShared S;
+    double *base = reinterpret_cast<double *>(raw);
+    S.xd = base;
+    S.y = S.xd + (size_t)nmax * p;
+    S.a = S.y + nmax;
+    S.t1 = S.a + nmax;
+    S.t2 = S.t1 + nmax;
+    S.t3 = S.t2 + nmax;
+    S.kx = S.t3 + nmax;
+    S.dx = S.kx + nmax;
+    S.xq = S.dx + nmax;
+    return S;
+}
+
+__device__ GpWork work_for_block(double *ws, int nmax, int ld) {
+    const size_t mat = (size_t)nmax * ld;
+    double *w = ws + (size_t)blockIdx.x * 6 * mat;
+    return GpWork{w, w + mat, w + 2 * mat, w + 3 * mat, w + 4 * mat, w + 5 * mat};
+}
+
+// ------------------------------------------------------------------ predict
+
+__global__ void __launch_bounds__(GP_THREADS)
+predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, double *mean,
+               double *s2, double *df, int32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
+    GpShared S = carve(smem_raw, nmax, p);
+    GpWork W = work_for_block(ws, nmax, ld);
+    __shared__ int s_loc, s_flag, s_chol;
+    __shared__ double red[GP_WARPS];
+    Blk b{(int)threadIdx.x, (int)threadIdx.x & 31, (int)threadIdx.x >> 5};
+    for (;;) {
+        if (b.tid == 0) s_loc = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t loc = s_loc;
+        __syncthreads();
+        if (loc >= a.M) break;
+        const int nm = a.n ? a.n[loc] : nmax;
+        int st = load_design(a, loc, nm, dv, S.xd, S.y, &s_flag, b);
+        double mu = CUDART_NAN, sv = CUDART_NAN, dfv = CUDART_NAN;
+        if (st == LAGP_OK) {
+            const double d = dv[loc], g = a.g;
+            for (int i = b.tid; i < p; i += GP_THREADS) S.xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
+            build_D(S.xd, nm, p, W.D, ld, b);
+            build_K(W.D, nm, ld, d, g, W.K, b);
+            for (int t = b.tid; t < nm; t += GP_THREADS) S.kx[t] = exp(-sqd(S.xq, S.xd + (size_t)t * p, p) / d);
+            __syncthreads();
+            if (!block_cholesky(W.K, W.L, nm, ld, &s_chol, b)) {
+                st = LAGP_ENOTPD;
+            } else {
+                if (b.warp == 0) warp_forward(W.L, ld, S.y, S.t1, nm, b.lane);   // z
+                if (b.warp == 1) warp_forward(W.L, ld, S.kx, S.t2, nm, b.lane);  // w
+                __syncthreads();
+                double m_p = 0.0, psi_p = 0.0, kk_p = 0.0;
+                for (int i = b.tid; i < nm; i += GP_THREADS) {
+                    m_p = fma(S.t2[i], S.t1[i], m_p);
+                    psi_p = fma(S.t1[i], S.t1[i], psi_p);
+                    kk_p = fma(S.t2[i], S.t2[i], kk_p);
+                }
+                mu = block_sum(m_p, red, b);
+                const double psi = block_sum(psi_p, red, b);
+                const double kk = block_sum(kk_p, red, b);
+                sv = psi * ((1.0 + g) - kk) / nm;
+                dfv = nm;
+            }
+        }
+        if (b.tid == 0) {
+            mean[loc] = mu;
+            s2[loc] = sv;
+            df[loc] = dfv;
+            status[loc] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------- MLE
+
+struct MleOut {
+    double *llik, *dllik, *d2llik;
+    int32_t *iters, *status;
+};
+
+__global__ void __launch_bounds__(GP_THREADS)
+mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *counter, double *ws,
+           MleOut o) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
+    GpShared S = carve(smem_raw, nmax, p);
+    GpWork W = work_for_block(ws, nmax, ld);
+    __shared__ int s_loc, s_flag, s_chol;
+    __shared__ double red[GP_WARPS];
+    Blk b{(int)threadIdx.x, (int)threadIdx.x & 31, (int)threadIdx.x >> 5};
+    for (;;) {
+        if (b.tid == 0) s_loc = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t loc = s_loc;
+        __syncthreads();
+        if (loc >= a.M) break;
+        const int nm = a.n ? a.n[loc] : nmax;
+        int st = load_design(a, loc, nm, dv, S.xd, S.y, &s_flag, b);
+        double l = CUDART_NAN, psi = 0.0;
+        Derivs dr{CUDART_NAN, CUDART_NAN, CUDART_NAN, CUDART_NAN};
+        int it = 0;
+        double d = dv[loc];
+        if (st == LAGP_OK) {
+            const double g = a.g;
+            d = fmin(fmax(d, dmin), dmax);
+            build_D(S.xd, nm, p, W.D, ld, b);
+            build_K(W.D, nm, ld, d, g, W.K, b);
+            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &l, &psi, b)) {
+                st = LAGP_ENOTPD;
+            } else {
+                dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
+                while (it < max_iter) {
+                    it++;
+                    double delta;
+                    if (dr.d2l < 0.0) delta = -dr.dl / dr.d2l;
+                    else delta = (dr.dl > 0.0) ? d : -0.5 * d;
+                    bool accepted = false;
+                    double dn = d, ln = l, psin = psi;
+                    for (int h = 0; h <= 20; h++) {
+                        dn = fmin(fmax(d + delta, dmin), dmax);
+                        build_K(W.D, nm, ld, dn, g, W.K, b);
+                        if (llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &ln, &psin, b) && ln >= l) {
+                            accepted = true;
+                            break;
+                        }
+                        delta *= 0.5;
+                    }
+                    if (!accepted) {
+                        // restore K, L, a at the current d
+                        build_K(W.D, nm, ld, d, g, W.K, b);
+                        llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &l, &psi, b);
+                        break;
+                    }
+                    const double step = fabs(dn - d);
+                    d = dn;
+                    l = ln;
+                    psi = psin;
+                    dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
+                    if (step < 1e-10 * d) break;
+                }
+            }
+        }
+        if (b.tid == 0) {
+            if (st == LAGP_OK) dv[loc] = d;
+            if (o.llik) o.llik[loc] = st == LAGP_OK ? l : CUDART_NAN;
+            if (o.dllik) o.dllik[loc] = st == LAGP_OK ? dr.dl : CUDART_NAN;
+            if (o.d2llik) o.d2llik[loc] = st == LAGP_OK ? dr.d2l : CUDART_NAN;
+            if (o.iters) o.iters[loc] = it;
+            o.status[loc] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+
+struct GradOut {
+    double *dmean_dd, *dmean_dg, *ds2_dd, *ds2_dg, *dllik_dd, *dllik_dg;
+    int32_t *status;
+};
+
+__global__ void __launch_bounds__(GP_THREADS)
+grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, GradOut o) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
+    GpShared S = carve(smem_raw, nmax, p);
+    GpWork W = work_for_block(ws, nmax, ld);
+    __shared__ int s_loc, s_flag, s_chol;
+    __shared__ double red[GP_WARPS];
+    Blk b{(int)threadIdx.x, (int)threadIdx.x & 31, (int)threadIdx.x >> 5};
+    for (;;) {
+        if (b.tid == 0) s_loc = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t loc = s_loc;
+        __syncthreads();
+        if (loc >= a.M) break;
+        const int nm = a.n ? a.n[loc] : nmax;
+        int st = load_design(a, loc, nm, dv, S.xd, S.y, &s_flag, b);
+        double r[6] = {CUDART_NAN, CUDART_NAN, CUDART_NAN, CUDART_NAN, CUDART_NAN, CUDART_NAN};
+        if (st == LAGP_OK) {
+            const double d = dv[loc], g = a.g, d2 = d * d;
+            for (int i = b.tid; i < p; i += GP_THREADS) S.xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
+            build_D(S.xd, nm, p, W.D, ld, b);
+            build_K(W.D, nm, ld, d, g, W.K, b);
+            double l, psi;
+            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &l, &psi, b)) {
+                st = LAGP_ENOTPD;
+            } else {
+                Derivs dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
+                // kx, kx_d = (Dx/d^2) kx ; b = K^{-1} kx (t1), K'a (t2), K'b (t3)
+                for (int t = b.tid; t < nm; t += GP_THREADS) {
+                    S.dx[t] = sqd(S.xq, S.xd + (size_t)t * p, p);
+                    S.kx[t] = exp(-S.dx[t] / d);
+                }
+                __syncthreads();
+                for (int i = b.tid; i < nm; i += GP_THREADS) {
+                    double s = 0.0;
+                    for (int k = 0; k < nm; k++) s = fma(W.Ki[(size_t)i * ld + k], S.kx[k], s);
+                    S.t1[i] = s;
+                }
+                __syncthreads();
+                for (int i = b.tid; i < nm; i += GP_THREADS) {
+                    double sa = 0.0, sb = 0.0;
+                    for (int k = 0; k < nm; k++) {
+                        double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
+                        double K1 = (W.D[(size_t)i * ld + k] / d2) * E;
+                        sa = fma(K1, S.a[k], sa);
+                        sb = fma(K1, S.t1[k], sb);
+                    }
+                    S.t2[i] = sa;
+                    S.t3[i] = sb;
+                }
+                __syncthreads();
+                double kxd_a = 0, bK1a = 0, aK1a = 0, kxd_b = 0, bK1b = 0, ba = 0, aa = 0, bb = 0, kk = 0;
+                for (int i = b.tid; i < nm; i += GP_THREADS) {
+                    const double kxi = S.kx[i];
+                    const double kxdi = (S.dx[i] / d2) * kxi;
+                    kxd_a = fma(kxdi, S.a[i], kxd_a);
+                    kxd_b = fma(kxdi, S.t1[i], kxd_b);
+                    bK1a = fma(S.t1[i], S.t2[i], bK1a);
+                    aK1a = fma(S.a[i], S.t2[i], aK1a);
+                    bK1b = fma(S.t1[i], S.t3[i], bK1b);
+                    ba = fma(S.t1[i], S.a[i], ba);
+                    aa = fma(S.a[i], S.a[i], aa);
+                    bb = fma(S.t1[i], S.t1[i], bb);
+                    kk = fma(kxi, S.t1[i], kk);
+                }
+                kxd_a = block_sum(kxd_a, red, b);
+                kxd_b = block_sum(kxd_b, red, b);
+                bK1a = block_sum(bK1a, red, b);
+                aK1a = block_sum(aK1a, red, b);
+                bK1b = block_sum(bK1b, red, b);
+                ba = block_sum(ba, red, b);
+                aa = block_sum(aa, red, b);
+                bb = block_sum(bb, red, b);
+                kk = block_sum(kk, red, b);
+                const double v = (1.0 + g) - kk;
+                r[0] = kxd_a - bK1a;
+                r[1] = -ba;
+                r[2] = (-aK1a * v + psi * (-2.0 * kxd_b + bK1b)) / nm;
+                r[3] = (-aa * v + psi * (1.0 + bb)) / nm;
+                r[4] = dr.dl;
+                r[5] = dr.dldg;
+            }
+        }
+        if (b.tid == 0) {
+            if (o.dmean_dd) o.dmean_dd[loc] = r[0];
+            if (o.dmean_dg) o.dmean_dg[loc] = r[1];
+            if (o.ds2_dd) o.ds2_dd[loc] = r[2];
+            if (o.ds2_dg) o.ds2_dg[loc] = r[3];
+            if (o.dllik_dd) o.dllik_dd[loc] = r[4];
+            if (o.dllik_dg) o.dllik_dg[loc] = r[5];
+            o.status[loc] = st;
+        }
+        __syncthreads();
+    }
+}
+
+struct GpLaunch {
+    int grid;
+    size_t smem;
+    double *ws;
+    int *counter;
+};
+
+template <typename Kern>
+lagp_status prepare(lagp_ctx *ctx, const GpArgs &a, Kern kern, GpLaunch &L) {
+    const int ld = (a.nmax + 31) & ~31;
+    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p) * 8 + 64;
+    if (L.smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "n_max x p too large");
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    int per_sm = 2;
+    int64_t grid = (int64_t)ctx->num_sms * per_sm;
+    if (grid > a.M) grid = a.M;
+    if (grid < 1) grid = 1;
+    L.grid = (int)grid;
+    L.ws = static_cast<double *>(lagp_ws(ctx, WS_GP_MAT, (size_t)grid * 6 * a.nmax * ld * 8 + 256));
+    L.counter = static_cast<int *>(lagp_ws(ctx, WS_ALC_COUNTER, 256));
+    if (!L.ws || !L.counter) return LAGP_ENOMEM;
+    LAGP_CUDA(ctx, cudaMemsetAsync(L.counter + 1, 0, sizeof(int), ctx->stream));
+    L.counter += 1;  // its own counter word
+    return LAGP_OK;
+}
+
+}  // namespace
+
+lagp_status launch_predict(lagp_ctx *ctx, const GpArgs &a, const double *d, double *mean,
+                           double *s2, double *df, int32_t *status) {
+    GpLaunch L;
+    LAGP_TRY(prepare(ctx, a, predict_kernel, L));
+    predict_kernel<<<L.grid, GP_THREADS, L.smem, ctx->stream>>>(a, d, L.counter, L.ws, mean, s2, df, status);
+    ctx->launches++;
+    LAGP_CUDA(ctx, cudaGetLastError());
+    return LAGP_OK;
+}
+
+lagp_status launch_mle(lagp_ctx *ctx, const GpArgs &a, double *d, double dmin, double dmax,
+                       int32_t max_iter, double *llik, double *dllik, double *d2llik,
+                       int32_t *iters, int32_t *status) {
+    GpLaunch L;
+    LAGP_TRY(prepare(ctx, a, mle_kernel, L));
+    MleOut o{llik, dllik, d2llik, iters, status};
+    mle_kernel<<<L.grid, GP_THREADS, L.smem, ctx->stream>>>(a, d, dmin, dmax, max_iter, L.counter, L.ws, o);
+    ctx->launches++;
+    LAGP_CUDA(ctx, cudaGetLastError());
+    return LAGP_OK;
+}
+
+lagp_status launch_predict_grad(lagp_ctx *ctx, const GpArgs &a, const double *d,
+                                double *dmean_dd, double *dmean_dg, double *ds2_dd,
+                                double *ds2_dg, double *dllik_dd, double *dllik_dg,
+                                int32_t *status) {
+    GpLaunch L;
+    LAGP_TRY(prepare(ctx, a, grad_kernel, L));
+    GradOut o{dmean_dd, dmean_dg, ds2_dd, ds2_dg, dllik_dd, dllik_dg, status};
+    grad_kernel<<<L.grid, GP_THREADS, L.smem, ctx->stream>>>(a, d, L.counter, L.ws, o);
+    ctx->launches++;
+    LAGP_CUDA(ctx, cudaGetLastError());
+    return LAGP_OK;
+}

@@ -1,0 +1,329 @@
+// C ABI entry points of liblagp.so: context management, argument checking,
+// workspace, and the whole-method host-buffer call (lagp_agp).
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lagp_internal.h"
+
+// ------------------------------------------------------------- status/errors
+
+lagp_status lagp_fail(lagp_ctx *ctx, lagp_status s, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+lagp_status lagp_cuda_check(lagp_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LAGP_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return lagp_fail(ctx, e == cudaErrorMemoryAllocation ? LAGP_ENOMEM : LAGP_ECUDA, m);
+}
+
+void *lagp_ws(lagp_ctx *ctx, WsSlot slot, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (ctx->ws_bytes[slot] >= bytes) return ctx->ws[slot];
+    // grow geometrically to limit reallocations
+    size_t want = bytes + bytes / 4;
+    if (ctx->ws[slot]) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->ws[slot]);
+        ctx->ws[slot] = nullptr;
+        ctx->ws_bytes[slot] = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char buf[160];
+        snprintf(buf, sizeof buf, "workspace slot %d: cudaMalloc(%zu) failed: %s", (int)slot, want,
+                 cudaGetErrorString(e));
+        ctx->err = buf;
+        return nullptr;
+    }
+    ctx->ws[slot] = p;
+    ctx->ws_bytes[slot] = want;
+    return p;
+}
+
+extern "C" {
+
+const char *lagp_status_string(lagp_status s) {
+    switch (s) {
+        case LAGP_OK: return "LAGP_OK";
+        case LAGP_EINVAL: return "LAGP_EINVAL";
+        case LAGP_ENOTPD: return "LAGP_ENOTPD";
+        case LAGP_ECUDA: return "LAGP_ECUDA";
+        case LAGP_ETIMEOUT: return "LAGP_ETIMEOUT";
+        case LAGP_ENOMEM: return "LAGP_ENOMEM";
+    }
+    return "LAGP_UNKNOWN";
+}
+
+lagp_status lagp_create(lagp_ctx **out, int device, void *cuda_stream) {
+    if (!out) return LAGP_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return LAGP_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return LAGP_EINVAL;
+    lagp_ctx *ctx = new (std::nothrow) lagp_ctx();
+    if (!ctx) return LAGP_ENOMEM;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaDeviceProp pr;
+    if (cudaSetDevice(device) != cudaSuccess || cudaGetDeviceProperties(&pr, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return LAGP_ECUDA;
+    }
+    ctx->num_sms = pr.multiProcessorCount;
+    ctx->smem_optin = pr.sharedMemPerBlockOptin;
+    *out = ctx;
+    return LAGP_OK;
+}
+
+lagp_status lagp_destroy(lagp_ctx *ctx) {
+    if (!ctx) return LAGP_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (int s = 0; s < WS_NSLOTS; s++)
+        if (ctx->ws[s]) cudaFree(ctx->ws[s]);
+    delete ctx;
+    return LAGP_OK;
+}
+
+lagp_status lagp_set_stream(lagp_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LAGP_OK;
+}
+
+const char *lagp_last_error(const lagp_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lagp_status lagp_get_tuning(const lagp_ctx *ctx, lagp_tuning *out) {
+    if (!ctx || !out) return LAGP_EINVAL;
+    *out = ctx->tuning;
+    return LAGP_OK;
+}
+
+lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in) {
+    if (!ctx || !in) return LAGP_EINVAL;
+    if (in->ctas_per_sm < 0 || in->ctas_per_sm > 32 || in->block_threads < 0 ||
+        in->block_threads > 1024 || (in->block_threads % 32) != 0 || in->rescore_max < 1 ||
+        in->rescore_max > 32 || !(in->rescore_rel >= 0.0) || !(in->rescore_rel < 1.0))
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_set_tuning: field out of range");
+    ctx->tuning = *in;
+    return LAGP_OK;
+}
+
+int64_t lagp_launch_count(const lagp_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+// --------------------------------------------------------------------- kNN
+
+static lagp_status check_design(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
+                                lagp_dtype dtype, const char *fn) {
+    if (!X) return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": X is NULL");
+    if (N < 1 || N >= (int64_t)INT32_MAX)
+        return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": N must be in [1, 2^31-1)");
+    if (p < 1 || p > 64) return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": p must be in [1, 64]");
+    if (dtype != LAGP_F64 && dtype != LAGP_F32)
+        return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": unknown dtype");
+    return LAGP_OK;
+}
+
+lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                     const void *Xref, int64_t M, const int32_t *Nprime, int32_t Nprime_max,
+                     int32_t *idx, int32_t *status) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_knn"));
+    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: M < 0");
+    if (M == 0) return LAGP_OK;
+    if (!Xref || !idx) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: NULL Xref or idx");
+    if (Nprime_max < 1 || Nprime_max > N)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: need 1 <= Nprime_max <= N");
+    if (Nprime_max > 4096)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: Nprime_max above the supported 4096");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_knn(ctx, X, N, p, dtype, Xref, M, Nprime, Nprime_max, idx, status);
+}
+
+// --------------------------------------------------------------- ALC search
+
+lagp_status lagp_alc_select(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
+                            lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
+                            const int32_t *Nprime, int32_t Nprime_max, int32_t n0,
+                            const int32_t *n, int32_t n_max, const double *d, double g,
+                            lagp_precision prec, int32_t *sel, double *alc, int32_t *status) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_alc_select"));
+    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: M < 0");
+    if (M == 0) return LAGP_OK;
+    if (!Xref || !idx || !d || !sel || !status)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: NULL required array");
+    if (Nprime_max < 1 || Nprime_max > N || Nprime_max > 4096)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: need 1 <= Nprime_max <= min(N, 4096)");
+    if (n0 < 1 || n_max < n0 || n_max > Nprime_max || n_max > 256)
+        return lagp_fail(ctx, LAGP_EINVAL,
+                         "lagp_alc_select: need 1 <= n0 <= n_max <= min(Nprime_max, 256)");
+    if (!(g >= 0.0) || !std::isfinite(g)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: g must be >= 0");
+    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: unknown precision");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    AlcArgs a{X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0, n, n_max, d, g, sel, alc, status};
+    return prec == LAGP_PREC_F64 ? launch_alc_f64(ctx, a) : launch_alc_f32(ctx, a);
+}
+
+// --------------------------------------------------------- predict / MLE
+
+static lagp_status check_gp(lagp_ctx *ctx, const GpArgs &a, const char *fn, bool need_ref) {
+    LAGP_TRY(check_design(ctx, a.X, a.N, a.p, a.dtype, fn));
+    if (a.M < 0) return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": M < 0");
+    if (a.M == 0) return LAGP_OK;
+    if (!a.Y || !a.sel || (need_ref && !a.Xref))
+        return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": NULL required array");
+    if (a.nmax < 1 || a.nmax > 256)
+        return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": need 1 <= n_max <= 256");
+    if (!(a.g >= 0.0) || !std::isfinite(a.g))
+        return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": g must be >= 0");
+    return LAGP_OK;
+}
+
+lagp_status lagp_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                         lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *sel,
+                         const int32_t *n, int32_t n_max, const double *d, double g,
+                         double *mean, double *s2, double *df, int32_t *status) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    GpArgs a{X, Y, N, p, dtype, Xref, M, sel, n, n_max, g};
+    LAGP_TRY(check_gp(ctx, a, "lagp_predict", true));
+    if (M == 0) return LAGP_OK;
+    if (!d || !mean || !s2 || !df || !status)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict: NULL output or d");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_predict(ctx, a, d, mean, s2, df, status);
+}
+
+lagp_status lagp_mle_step(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                          lagp_dtype dtype, int64_t M, const int32_t *sel, const int32_t *n,
+                          int32_t n_max, double *d, double g, double dmin, double dmax,
+                          int32_t max_iter, double *llik, double *dllik, double *d2llik,
+                          int32_t *iters, int32_t *status) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    GpArgs a{X, Y, N, p, dtype, nullptr, M, sel, n, n_max, g};
+    LAGP_TRY(check_gp(ctx, a, "lagp_mle_step", false));
+    if (M == 0) return LAGP_OK;
+    if (!d || !status) return lagp_fail(ctx, LAGP_EINVAL, "lagp_mle_step: NULL d or status");
+    if (!(dmin > 0.0) || !(dmax >= dmin) || !std::isfinite(dmax) || max_iter < 0 || max_iter > 1000)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_mle_step: need 0 < dmin <= dmax, 0 <= max_iter <= 1000");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_mle(ctx, a, d, dmin, dmax, max_iter, llik, dllik, d2llik, iters, status);
+}
+
+lagp_status lagp_predict_grad(lagp_ctx *ctx, const void *X, const void *Y, int64_t N,
+                              int32_t p, lagp_dtype dtype, const void *Xref, int64_t M,
+                              const int32_t *sel, const int32_t *n, int32_t n_max,
+                              const double *d, double g, double *dmean_dd, double *dmean_dg,
+                              double *ds2_dd, double *ds2_dg, double *dllik_dd,
+                              double *dllik_dg, int32_t *status) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    GpArgs a{X, Y, N, p, dtype, Xref, M, sel, n, n_max, g};
+    LAGP_TRY(check_gp(ctx, a, "lagp_predict_grad", true));
+    if (M == 0) return LAGP_OK;
+    if (!d || !status) return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_grad: NULL d or status");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_predict_grad(ctx, a, d, dmean_dd, dmean_dg, ds2_dd, ds2_dg, dllik_dd, dllik_dg,
+                               status);
+}
+
+// ------------------------------------------------- whole method, host buffers
+
+lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                     lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *Nprime,
+                     int32_t Nprime_max, int32_t n0, const int32_t *n, int32_t n_max,
+                     double d0, double g, lagp_precision prec, int32_t do_mle, double dmin,
+                     double dmax, int32_t max_iter, double *mean, double *s2, double *df,
+                     double *d_out, int32_t *status) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_agp"));
+    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: M < 0");
+    if (M == 0) return LAGP_OK;
+    if (!Y || !Xref || !mean || !s2 || !df || !status)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: NULL required array");
+    if (!(d0 > 0.0)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: d0 must be > 0");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+
+    const size_t es = dtype == LAGP_F64 ? 8 : 4;
+    // device layout inside one workspace slot, each region 256-byte aligned
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t oX = 0, oY = oX + al(N * p * es), oR = oY + al(N * es), oNp = oR + al(M * p * es);
+    size_t on = oNp + al(M * 4), oIdx = on + al(M * 4), oSel = oIdx + al(M * (size_t)Nprime_max * 4);
+    size_t od = oSel + al(M * (size_t)n_max * 4), oMean = od + al(M * 8), oS2 = oMean + al(M * 8);
+    size_t oDf = oS2 + al(M * 8), oSt = oDf + al(M * 8), oSt2 = oSt + al(M * 4), oSt3 = oSt2 + al(M * 4),
+           oSt4 = oSt3 + al(M * 4), total = oSt4 + al(M * 4);
+    char *base = static_cast<char *>(lagp_ws(ctx, WS_AGP_IO, total));
+    if (!base) return LAGP_ENOMEM;
+    void *dX = base + oX, *dY = base + oY, *dR = base + oR;
+    int32_t *dNp = Nprime ? reinterpret_cast<int32_t *>(base + oNp) : nullptr;
+    int32_t *dn = n ? reinterpret_cast<int32_t *>(base + on) : nullptr;
+    int32_t *dIdx = reinterpret_cast<int32_t *>(base + oIdx);
+    int32_t *dSel = reinterpret_cast<int32_t *>(base + oSel);
+    double *dd = reinterpret_cast<double *>(base + od);
+    double *dMean = reinterpret_cast<double *>(base + oMean);
+    double *dS2 = reinterpret_cast<double *>(base + oS2);
+    double *dDf = reinterpret_cast<double *>(base + oDf);
+    int32_t *dSt = reinterpret_cast<int32_t *>(base + oSt);
+    int32_t *dSt2 = reinterpret_cast<int32_t *>(base + oSt2);
+    int32_t *dSt3 = reinterpret_cast<int32_t *>(base + oSt3);
+    int32_t *dSt4 = reinterpret_cast<int32_t *>(base + oSt4);
+    cudaStream_t st = ctx->stream;
+
+    LAGP_CUDA(ctx, cudaMemcpyAsync(dX, X, N * p * es, cudaMemcpyHostToDevice, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(dY, Y, N * es, cudaMemcpyHostToDevice, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(dR, Xref, M * p * es, cudaMemcpyHostToDevice, st));
+    if (Nprime) LAGP_CUDA(ctx, cudaMemcpyAsync(dNp, Nprime, M * 4, cudaMemcpyHostToDevice, st));
+    if (n) LAGP_CUDA(ctx, cudaMemcpyAsync(dn, n, M * 4, cudaMemcpyHostToDevice, st));
+    // d starts at d0 everywhere: fill on the host side of a small staging copy
+    {
+        std::vector<double> h(M, d0);
+        LAGP_CUDA(ctx, cudaMemcpyAsync(dd, h.data(), M * 8, cudaMemcpyHostToDevice, st));
+        LAGP_CUDA(ctx, cudaStreamSynchronize(st));  // h leaves scope
+    }
+    LAGP_TRY(lagp_knn(ctx, dX, N, p, dtype, dR, M, dNp, Nprime_max, dIdx, dSt4));
+    LAGP_TRY(lagp_alc_select(ctx, dX, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn, n_max,
+                             dd, g, prec, dSel, nullptr, dSt));
+    if (do_mle) {
+        LAGP_TRY(lagp_mle_step(ctx, dX, dY, N, p, dtype, M, dSel, dn, n_max, dd, g, dmin, dmax,
+                               max_iter, nullptr, nullptr, nullptr, nullptr, dSt2));
+    } else {
+        LAGP_CUDA(ctx, cudaMemsetAsync(dSt2, 0, M * 4, st));
+    }
+    LAGP_TRY(lagp_predict(ctx, dX, dY, N, p, dtype, dR, M, dSel, dn, n_max, dd, g, dMean, dS2,
+                          dDf, dSt3));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(mean, dMean, M * 8, cudaMemcpyDeviceToHost, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(s2, dS2, M * 8, cudaMemcpyDeviceToHost, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(df, dDf, M * 8, cudaMemcpyDeviceToHost, st));
+    if (d_out) LAGP_CUDA(ctx, cudaMemcpyAsync(d_out, dd, M * 8, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> s1(M), s2v(M), s3(M), s4(M);
+    LAGP_CUDA(ctx, cudaMemcpyAsync(s4.data(), dSt4, M * 4, cudaMemcpyDeviceToHost, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(s1.data(), dSt, M * 4, cudaMemcpyDeviceToHost, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(s2v.data(), dSt2, M * 4, cudaMemcpyDeviceToHost, st));
+    LAGP_CUDA(ctx, cudaMemcpyAsync(s3.data(), dSt3, M * 4, cudaMemcpyDeviceToHost, st));
+    LAGP_CUDA(ctx, cudaStreamSynchronize(st));
+    // first failing stage wins: kNN, selection, MLE, prediction
+    for (int64_t m = 0; m < M; m++)
+        status[m] = s4[m] != LAGP_OK ? s4[m] : s1[m] != LAGP_OK ? s1[m] : s2v[m] != LAGP_OK ? s2v[m] : s3[m];
+    return LAGP_OK;
+}
+
+}  // extern "C"

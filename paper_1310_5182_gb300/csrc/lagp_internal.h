@@ -1,0 +1,102 @@
+// Internal declarations shared by the translation units of liblagp.so:
+// the context, its workspace, and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lagp.h"
+
+// Workspace slots owned by a context; each grows on demand.
+enum WsSlot {
+    WS_KNN_X32 = 0,   // FP32 copy of the design for kNN screening
+    WS_KNN_CAND,      // kNN per-query candidate rows
+    WS_KNN_META,      // kNN per-query counters / thresholds / flags
+    WS_ALC_PANEL,     // ALC per-CTA candidate panel (F64 kernel values or F32 whitened U)
+    WS_ALC_STATE,     // ALC per-CTA FP64 state (K^{-1}, vectors)
+    WS_ALC_COUNTER,   // persistent-grid work counters
+    WS_GP_MAT,        // predict / MLE per-CTA matrices
+    WS_AGP_IO,        // lagp_agp device copies of inputs and outputs
+    WS_NSLOTS
+};
+
+struct lagp_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    void *ws[WS_NSLOTS] = {};
+    size_t ws_bytes[WS_NSLOTS] = {};
+    std::string err;
+    lagp_tuning tuning = {0, 0, 8, 0.05};
+    int64_t launches = 0;
+};
+
+// status helpers (lagp_api.cu)
+lagp_status lagp_fail(lagp_ctx *ctx, lagp_status s, const std::string &msg);
+lagp_status lagp_cuda_check(lagp_ctx *ctx, cudaError_t e, const char *what);
+// returns nullptr and sets the error on failure
+void *lagp_ws(lagp_ctx *ctx, WsSlot slot, size_t bytes);
+
+#define LAGP_TRY(expr)                       \
+    do {                                     \
+        lagp_status _s = (expr);             \
+        if (_s != LAGP_OK) return _s;        \
+    } while (0)
+#define LAGP_CUDA(ctx, expr) LAGP_TRY(lagp_cuda_check((ctx), (expr), #expr))
+
+// ----------------------------------------------------------------- launchers
+// Each launcher validates nothing (lagp_api.cu does), enqueues on ctx->stream,
+// adds its kernel count to ctx->launches and returns a CUDA error status.
+
+lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtype dtype,
+                       const void *Xref, int64_t M, const int32_t *Np, int32_t Npmax,
+                       int32_t *idx, int32_t *status);
+
+struct AlcArgs {
+    const void *X;
+    int64_t N;
+    int p;
+    lagp_dtype dtype;
+    const void *Xref;
+    int64_t M;
+    const int32_t *idx;
+    const int32_t *Np;  // may be null
+    int32_t Npmax;
+    int32_t n0;
+    const int32_t *n;   // may be null
+    int32_t nmax;
+    const double *d;
+    double g;
+    int32_t *sel;
+    double *alc;        // may be null
+    int32_t *status;
+};
+
+lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a);
+lagp_status launch_alc_f32(lagp_ctx *ctx, const AlcArgs &a);
+
+struct GpArgs {
+    const void *X;
+    const void *Y;
+    int64_t N;
+    int p;
+    lagp_dtype dtype;
+    const void *Xref;   // predict / grad only
+    int64_t M;
+    const int32_t *sel;
+    const int32_t *n;   // may be null
+    int32_t nmax;
+    double g;
+};
+
+lagp_status launch_predict(lagp_ctx *ctx, const GpArgs &a, const double *d, double *mean,
+                           double *s2, double *df, int32_t *status);
+lagp_status launch_mle(lagp_ctx *ctx, const GpArgs &a, double *d, double dmin, double dmax,
+                       int32_t max_iter, double *llik, double *dllik, double *d2llik,
+                       int32_t *iters, int32_t *status);
+lagp_status launch_predict_grad(lagp_ctx *ctx, const GpArgs &a, const double *d,
+                                double *dmean_dd, double *dmean_dg, double *ds2_dd,
+                                double *ds2_dg, double *dllik_dd, double *dllik_dg,
+                                int32_t *status);

@@ -1,0 +1,306 @@
+"""Thin Python binding of liblagp.so (C ABI declared in include/lagp.h).
+
+Argument marshalling only: every step of local approximate GP regression runs
+in the library's CUDA kernels.  Device arrays are PyTorch CUDA tensors (memory
+and streams come from PyTorch); work is enqueued on the current PyTorch
+stream of the tensors' device.  There is no CPU fallback: if liblagp.so is
+missing or cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblagp.so")
+
+LAGP_OK, LAGP_EINVAL, LAGP_ENOTPD, LAGP_ECUDA, LAGP_ETIMEOUT, LAGP_ENOMEM = range(6)
+LAGP_F64, LAGP_F32 = 0, 1
+LAGP_PREC_F64, LAGP_PREC_F32BULK = 0, 1
+_PREC = {"f64": LAGP_PREC_F64, "f32bulk": LAGP_PREC_F32BULK}
+
+
+class LagpError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        self.code = code
+        super().__init__(f"{fn} failed: {_STATUS.get(code, code)}: {msg}")
+
+
+_STATUS = {0: "LAGP_OK", 1: "LAGP_EINVAL", 2: "LAGP_ENOTPD", 3: "LAGP_ECUDA", 4: "LAGP_ETIMEOUT",
+           5: "LAGP_ENOMEM"}
+
+
+class lagp_tuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("rescore_max", ctypes.c_int32), ("rescore_rel", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.lagp_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P]
+    lib.lagp_destroy.argtypes = [P]
+    lib.lagp_set_stream.argtypes = [P, P]
+    lib.lagp_last_error.argtypes = [P]
+    lib.lagp_last_error.restype = ctypes.c_char_p
+    lib.lagp_status_string.argtypes = [ctypes.c_int]
+    lib.lagp_status_string.restype = ctypes.c_char_p
+    lib.lagp_get_tuning.argtypes = [P, ctypes.POINTER(lagp_tuning)]
+    lib.lagp_set_tuning.argtypes = [P, ctypes.POINTER(lagp_tuning)]
+    lib.lagp_launch_count.argtypes = [P]
+    lib.lagp_launch_count.restype = I64
+    lib.lagp_knn.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P, I32, P, P]
+    lib.lagp_alc_select.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, I32, P, I32, P,
+                                    D, ctypes.c_int, P, P, P]
+    lib.lagp_predict.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P, P, P]
+    lib.lagp_mle_step.argtypes = [P, P, P, I64, I32, ctypes.c_int, I64, P, P, I32, P, D, D, D, I32,
+                                  P, P, P, P, P]
+    lib.lagp_predict_grad.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P,
+                                      P, P, P, P, P]
+    lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
+                             ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
+    for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
+              "lagp_knn", "lagp_alc_select", "lagp_predict", "lagp_mle_step", "lagp_predict_grad",
+              "lagp_agp"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+_ctx_lock = threading.Lock()
+_ctxs: dict[int, ctypes.c_void_p] = {}
+
+
+def library():
+    """The loaded ctypes library handle."""
+    return _lib
+
+
+def context(device: int | torch.device | None = None):
+    """The library context for a CUDA device, bound to PyTorch's current
+    stream on that device."""
+    if device is None:
+        device = torch.cuda.current_device()
+    dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    with _ctx_lock:
+        ctx = _ctxs.get(idx)
+        if ctx is None:
+            ctx = ctypes.c_void_p()
+            stream = torch.cuda.current_stream(idx).cuda_stream
+            rc = _lib.lagp_create(ctypes.byref(ctx), idx, ctypes.c_void_p(stream))
+            if rc != LAGP_OK:
+                raise LagpError("lagp_create", rc, "could not create a context")
+            _ctxs[idx] = ctx
+    _check(_lib.lagp_set_stream(ctx, ctypes.c_void_p(torch.cuda.current_stream(idx).cuda_stream)),
+           ctx, "lagp_set_stream")
+    return ctx
+
+
+def _check(rc, ctx, fn):
+    if rc != LAGP_OK:
+        msg = _lib.lagp_last_error(ctx) if ctx else b""
+        raise LagpError(fn, rc, (msg or b"").decode())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return LAGP_F64
+    if t.dtype == torch.float32:
+        return LAGP_F32
+    raise TypeError(f"coordinates must be float64 or float32, not {t.dtype}")
+
+
+def _dev(t: torch.Tensor, name, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _opt_i32(v, M, device, name):
+    """None -> NULL pointer; int / array -> int32 CUDA tensor of length M."""
+    if v is None:
+        return None, None
+    t = torch.as_tensor(v, dtype=torch.int32, device=device)
+    if t.dim() == 0:
+        t = t.expand(M)
+    t = t.contiguous()
+    if t.numel() != M:
+        raise ValueError(f"{name} must have M = {M} entries")
+    return t, ctypes.c_void_p(t.data_ptr())
+
+
+def _per_loc_f64(v, M, device):
+    t = torch.as_tensor(v, dtype=torch.float64, device=device)
+    if t.dim() == 0:
+        t = t.expand(M)
+    return t.contiguous().clone() if t.numel() == M else _bad(f"expected M = {M} values")
+
+
+def _bad(msg):
+    raise ValueError(msg)
+
+
+def _ptr_or_null(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def get_tuning(device=None) -> lagp_tuning:
+    ctx = context(device)
+    t = lagp_tuning()
+    _check(_lib.lagp_get_tuning(ctx, ctypes.byref(t)), ctx, "lagp_get_tuning")
+    return t
+
+
+def set_tuning(device=None, **fields):
+    ctx = context(device)
+    t = get_tuning(device)
+    for k, v in fields.items():
+        setattr(t, k, v)
+    _check(_lib.lagp_set_tuning(ctx, ctypes.byref(t)), ctx, "lagp_set_tuning")
+
+
+def launch_count(device=None) -> int:
+    return int(_lib.lagp_launch_count(context(device)))
+
+
+def lagp_knn(X: torch.Tensor, Xref: torch.Tensor, Nprime_max: int, Nprime=None):
+    """a1: exact N'-nearest neighbours.  Returns (idx [M, Nprime_max] int32,
+    status [M] int32)."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M = Xref.shape[0]
+    if Xref.dtype != X.dtype or Xref.shape[1] != p:
+        raise ValueError("Xref must match X in dtype and p")
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    idx = torch.empty((M, Nprime_max), dtype=torch.int32, device=X.device)
+    status = torch.empty(M, dtype=torch.int32, device=X.device)
+    if M:
+        _check(_lib.lagp_knn(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref"), M, Npp,
+                             int(Nprime_max), _dev(idx, "idx"), _dev(status, "status")),
+               ctx, "lagp_knn")
+    return idx, status
+
+
+def lagp_alc_select(X, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, n_max=None,
+                    want_alc=False):
+    """a2..a6: greedy ALC local designs.  n, d: scalars or per-location
+    arrays.  Returns dict(sel [M, n_max], status [M], alc [M, n_max] or None)."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, Npmax = idx.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    if n_max is None:
+        n_max = int(nt.max().item()) if nt is not None and M else int(n)
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    dt = _per_loc_f64(d, M, X.device)
+    sel = torch.empty((M, n_max), dtype=torch.int32, device=X.device)
+    status = torch.empty(M, dtype=torch.int32, device=X.device)
+    alc = torch.empty((M, n_max), dtype=torch.float64, device=X.device) if want_alc else None
+    if M:
+        _check(_lib.lagp_alc_select(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref"), M,
+                                    _dev(idx, "idx", torch.int32), Npp, Npmax, int(n0), npp,
+                                    int(n_max), _dev(dt, "d"), float(g), _PREC[prec],
+                                    _dev(sel, "sel"), _ptr_or_null(alc), _dev(status, "status")),
+               ctx, "lagp_alc_select")
+    return dict(sel=sel, status=status, alc=alc)
+
+
+def lagp_predict(X, Y, Xref, sel, n, d, g):
+    """a7: local predictive mean, scale and degrees of freedom."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, n_max = sel.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    dt = _per_loc_f64(d, M, X.device)
+    out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in ("mean", "s2", "df")}
+    status = torch.empty(M, dtype=torch.int32, device=X.device)
+    if M:
+        _check(_lib.lagp_predict(ctx, _dev(X, "X"), _dev(Y, "Y", X.dtype), N, p, _dtype_code(X),
+                                 _dev(Xref, "Xref", X.dtype), M, _dev(sel, "sel", torch.int32), npp,
+                                 n_max, _dev(dt, "d"), float(g), _dev(out["mean"], "mean"),
+                                 _dev(out["s2"], "s2"), _dev(out["df"], "df"), _dev(status, "status")),
+               ctx, "lagp_predict")
+    out["status"] = status
+    return out
+
+
+def lagp_mle_step(X, Y, sel, n, d0, g, dmin, dmax, max_iter):
+    """a8: per-location Newton MLE of d.  Returns dict(d, llik, dllik,
+    d2llik, iters, status)."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, n_max = sel.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    d = _per_loc_f64(d0, M, X.device)
+    out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in ("llik", "dllik", "d2llik")}
+    iters = torch.empty(M, dtype=torch.int32, device=X.device)
+    status = torch.empty(M, dtype=torch.int32, device=X.device)
+    if M:
+        _check(_lib.lagp_mle_step(ctx, _dev(X, "X"), _dev(Y, "Y", X.dtype), N, p, _dtype_code(X), M,
+                                  _dev(sel, "sel", torch.int32), npp, n_max, _dev(d, "d"), float(g),
+                                  float(dmin), float(dmax), int(max_iter), _dev(out["llik"], "llik"),
+                                  _dev(out["dllik"], "dllik"), _dev(out["d2llik"], "d2llik"),
+                                  _dev(iters, "iters"), _dev(status, "status")),
+               ctx, "lagp_mle_step")
+    out.update(d=d, iters=iters, status=status)
+    return out
+
+
+def lagp_predict_grad(X, Y, Xref, sel, n, d, g):
+    """Adjoint: d/dd, d/dg of mean, s2 and the log-likelihood, per location."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, n_max = sel.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    dt = _per_loc_f64(d, M, X.device)
+    keys = ("dmean_dd", "dmean_dg", "ds2_dd", "ds2_dg", "dllik_dd", "dllik_dg")
+    out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in keys}
+    status = torch.empty(M, dtype=torch.int32, device=X.device)
+    if M:
+        _check(_lib.lagp_predict_grad(ctx, _dev(X, "X"), _dev(Y, "Y", X.dtype), N, p, _dtype_code(X),
+                                      _dev(Xref, "Xref", X.dtype), M, _dev(sel, "sel", torch.int32),
+                                      npp, n_max, _dev(dt, "d"), float(g),
+                                      *[_dev(out[k], k) for k in keys], _dev(status, "status")),
+               ctx, "lagp_predict_grad")
+    out["status"] = status
+    return out
+
+
+def lagp_agp(X, Y, Xref, n0, n, Nprime, d0, g, prec="f32bulk", mle=None, device=0):
+    """The whole method on HOST arrays (numpy or CPU tensors): kNN -> ALC ->
+    optional MLE (mle = (dmin, dmax, max_iter)) -> predict.  Inputs are copied
+    to the GPU and results back inside the call.  Returns numpy arrays."""
+    ctx = context(device)
+    X = np.ascontiguousarray(X)
+    if X.dtype not in (np.float64, np.float32):
+        raise TypeError("X must be float64 or float32")
+    Y = np.ascontiguousarray(Y, dtype=X.dtype)
+    Xref = np.ascontiguousarray(Xref, dtype=X.dtype)
+    N, p = X.shape
+    M = Xref.shape[0]
+    n_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int32), (M,)))
+    Np_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(Nprime, np.int32), (M,)))
+    out = {k: np.empty(M, np.float64) for k in ("mean", "s2", "df", "d")}
+    status = np.empty(M, np.int32)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    dmin, dmax, it = mle if mle is not None else (1e-3, 20.0, 0)
+    _check(_lib.lagp_agp(ctx, ptr(X), ptr(Y), N, p, LAGP_F64 if X.dtype == np.float64 else LAGP_F32,
+                         ptr(Xref), M, ptr(Np_arr), int(Np_arr.max()) if M else 1, int(n0), ptr(n_arr),
+                         int(n_arr.max()) if M else int(n0), float(d0), float(g), _PREC[prec],
+                         1 if mle is not None else 0, float(dmin), float(dmax), int(it),
+                         ptr(out["mean"]), ptr(out["s2"]), ptr(out["df"]), ptr(out["d"]), ptr(status)),
+           ctx, "lagp_agp")
+    out["status"] = status
+    return out
