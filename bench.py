@@ -1,0 +1,337 @@
+"""Benchmark: local approximate GP predictions per second on one batch of
+reference locations (kNN -> greedy ALC local designs -> local prediction).
+
+Default workload: the 8-d borehole configuration, N = 100,000 design points,
+M = 10,000 reference locations per GPU, (n0, n, N') = (6, 50, 1000), d = 2,
+g = 1e-6, synthetic (seeded) data.  One step = one pass of the whole hot path
+over the batch: kNN (a1), ALC search (a2-a6, FP32-bulk form), prediction (a7).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  For N > 1 launch under torchrun; each rank
+predicts its own M locations (weak scaling) and the slowest rank's time sets
+the aggregate rate.  --impl reference times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "local predictions/sec (n=50, N'=1000)"
+WORKLOAD = "borehole8d_N100000_M10000_n50_Nprime1000"
+L2_FLUSH_BYTES = 512 << 20  # > the 126 MiB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["f32bulk", "f64"], default="f32bulk")
+    ap.add_argument("--no-f64", action="store_true", help="skip the FP64-plain comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--M", type=int, default=None,
+                    help="reference locations per GPU (default: the workload's 10,000; smaller "
+                         "values are for profiler captures, not bench lines)")
+    return ap.parse_args()
+
+
+def workload_for_rank(rank: int, M=None):
+    """The borehole workload; rank r > 0 draws its own reference locations."""
+    w = W.c2_borehole_100k() if M is None else W.c2_borehole_100k(M=M)
+    if rank > 0:
+        rng = np.random.default_rng(1_000_003 + rank)
+        xr = rng.uniform(0.0, 1.0, size=w.Xref.shape)
+        mu, sd = w.meta["y_mean"], w.meta["y_sd"]
+        w.Xref = xr.astype(w.X.dtype)
+        w.truth = (W.borehole_f(xr) - mu) / sd
+    return w
+
+
+def work_per_location(n0, n, Np):
+    """Algorithmic counts per location: ALC candidate evaluations of the
+    greedy search, E = sum_{j=n0}^{n-1} (N' - j), and the bytes of the
+    whitened candidate panel U that the FP32-bulk screen reads and writes,
+    sum_{j=0}^{n-2} (N' j + N') * 4 (one FP32 column read per design row and
+    one column written per step)."""
+    E = sum(Np - j for j in range(n0, n))
+    U_bytes = sum((Np * j + Np) * 4 for j in range(0, n - 1))
+    return E, U_bytes
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- oracle legs
+
+def oracle_sample(w, S, seed=0):
+    """Time the FP64 oracle (all host cores, OpenMP over locations) on S
+    seeded reference locations of the workload.  Returns (seconds, cores)."""
+    from oracle import oracle as O
+    O.build()
+    cores = O.set_threads(os.cpu_count() or 1)
+    samp = np.random.default_rng(seed).choice(w.M, S, replace=False)
+    t0 = time.perf_counter()
+    O.run_pipeline(w.X, w.Y, w.Xref[samp], w.n0, w.n[samp], int(w.Np[0]), w.d, w.g)
+    return time.perf_counter() - t0, cores
+
+
+def run_reference(args, rank, world):
+    w = workload_for_rank(0)
+    S = 512
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(w, 16, seed=99)
+    times, cores = [], 1
+    for k in range(args.steps):
+        t, cores = oracle_sample(w, S, seed=k)
+        times.append(t)
+    sec = sum(times)
+    value = S * args.steps / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "predictions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": S, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "predictions/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{S} seeded reference locations per step of the {WORKLOAD} workload"},
+        "e2e": {"value": value, "unit": "predictions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1310_5182_gb300 as L
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload_for_rank(rank, args.M)
+    n0, n, Np, d, g = w.n0, int(w.n[0]), int(w.Np[0]), w.d, w.g
+    X = torch.from_numpy(w.X).to(dev)
+    Y = torch.from_numpy(w.Y).to(dev)
+    Xr = torch.from_numpy(w.Xref).to(dev)
+    M = w.M
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec, ev=None):
+        idx, _ = L.lagp_knn(X, Xr, Np)
+        if ev is not None:
+            ev[0].record(stream)
+        s = L.lagp_alc_select(X, Xr, idx, n0, n, d, g, prec=prec)
+        if ev is not None:
+            ev[1].record(stream)
+        p = L.lagp_predict(X, Y, Xr, s["sel"], n, d, g)
+        return s, p
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(args.prec)
+    barrier()
+    clk = ClockSampler(local_rank) if rank == 0 else None
+    launches0 = L.launch_count(dev)
+    step_ms, alc_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()  # evict the design and panels from L2 between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        s, p = step(args.prec, (a0, a1))
+        e1.record(stream)
+        barrier()
+        step_ms.append(e0.elapsed_time(e1))
+        alc_ms.append(a0.elapsed_time(a1))
+    launches = (L.launch_count(dev) - launches0)
+    clocks = clk.stop() if clk else None
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = M * world * args.steps / t_max
+
+    # parity spot-check of this run's output: statuses and RMSE to the truth
+    st = s["status"].cpu().numpy()
+    mean = p["mean"].cpu().numpy()
+    rmse = float(np.sqrt(np.mean((mean - w.truth) ** 2)))
+
+    # FP64 plain form on the same batch (the "vs FP64" comparison)
+    f64 = None
+    if not args.no_f64 and args.prec != "f64":
+        f64_ms, f64_alc = [], []
+        for it in range(2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            s64, p64 = step("f64", (a0, a1))
+            e1.record(stream)
+            barrier()
+            if it > 0:
+                f64_ms.append(e0.elapsed_time(e1))
+                f64_alc.append(a0.elapsed_time(a1))
+        sel_same = float((s64["sel"] == s["sel"]).all(dim=1).float().mean().item())
+        rmse64 = float(np.sqrt(np.mean((p64["mean"].cpu().numpy() - w.truth) ** 2)))
+        f64 = {"value": M / (f64_ms[0] / 1e3), "unit": "predictions/s", "ms_per_step": f64_ms[0],
+               "alc_kernel_ms": f64_alc[0], "rmse": rmse64,
+               "speedup_f32bulk_over_f64": (M / (t_local / args.steps)) / (M / (f64_ms[0] / 1e3)),
+               "identical_designs_frac": sel_same}
+
+    # end to end through the public host-buffer call (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        Xh, Yh, Xrh = pin(w.X), pin(w.Y), pin(w.Xref)
+        L.lagp_agp(Xh, Yh, Xrh, n0, n, Np, d, g, prec=args.prec, device=local_rank)  # warm
+        e2e_s = []
+        for _ in range(max(1, min(args.steps, 3))):
+            barrier()
+            t0 = time.perf_counter()
+            L.lagp_agp(Xh, Yh, Xrh, n0, n, Np, d, g, prec=args.prec, device=local_rank)
+            e2e_s.append(time.perf_counter() - t0)
+        te = torch.tensor([statistics.mean(e2e_s)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": M * world / float(te.item()), "unit": "predictions/s",
+               "h2d_bytes_per_step": Xh.nbytes + Yh.nbytes + Xrh.nbytes + 2 * M * 4,
+               "d2h_bytes_per_step": 4 * M * 8 + 4 * M * 4}
+
+    if rank != 0:
+        return
+    E, U_bytes = work_per_location(n0, n, Np)
+    alc_avg = statistics.mean(alc_ms) / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = M * U_bytes / alc_avg / 1e9
+    roofline = {"bound": "hbm", "kernel": "alc_f32_kernel", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": M * U_bytes}
+    cpu = None
+    if not args.no_cpu and world == 1:
+        S = 1024
+        sec, cores = oracle_sample(w, S)
+        cpu = {"value": S / sec, "unit": "predictions/s", "cores": cores, "kind": "oracle",
+               "sample": f"{S} seeded reference locations of the same workload (FP64 C oracle, "
+                         f"OpenMP over locations), {sec:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "predictions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": w.N, "M_per_gpu": M, "p": w.p, "n0": n0, "n": n,
+                   "Nprime": Np, "d": d, "g": g, "prec": args.prec,
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "cand_evals_per_sec": M * world * E / alc_avg,
+        "alc_kernel_ms": 1e3 * alc_avg,
+        "rmse_vs_truth": rmse, "status_ok_frac": float((st == 0).mean()),
+        "f64_plain": f64,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

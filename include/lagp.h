@@ -74,9 +74,13 @@ typedef struct {
     int32_t block_threads;  /* threads per CTA of the ALC kernels */
     int32_t rescore_max;    /* F32BULK: most candidates re-scored in FP64 per
                                step, 1..32 (default 8) */
-    double rescore_rel;     /* F32BULK: a candidate is re-scored in FP64 when
-                               its FP32 score is within this relative margin
-                               of the FP32 maximum (default 0.05) */
+    double rescore_rel;     /* F32BULK: cap of the contender margin (default
+                               0.5).  A candidate is re-scored in FP64 when its
+                               FP32 score is within the margin of the FP32
+                               maximum; the margin is 8x the largest relative
+                               FP32-vs-FP64 score error observed on earlier
+                               re-scores (decaying 0.75x per step), at least
+                               0.02 and at most rescore_rel */
 } lagp_tuning;
 
 /* Create a context on CUDA device `device` that enqueues on `cuda_stream`

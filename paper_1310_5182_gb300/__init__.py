@@ -2,20 +2,20 @@
 with greedy ALC local designs (Gramacy, Niemi & Weiss, arXiv:1310.5182).
 
 The compute path is liblagp.so (hand-written CUDA kernels behind the C ABI of
-include/lagp.h); this package is its thin Python binding.  Importing the
-binding requires the built library: there is no CPU fallback.
+include/lagp.h); the binding in .lagp marshals arguments to it.  The binding
+is loaded on first use of any of its names, and raises ImportError if the
+library has not been built: there is no CPU fallback.  The build module
+(paper_1310_5182_gb300.build) imports without the library.
 """
-from .lagp import (  # noqa: F401
-    LagpError,
-    context,
-    get_tuning,
-    lagp_agp,
-    lagp_alc_select,
-    lagp_knn,
-    lagp_mle_step,
-    lagp_predict,
-    lagp_predict_grad,
-    launch_count,
-    library,
-    set_tuning,
-)
+_BINDING = ("LagpError", "context", "get_tuning", "lagp_agp", "lagp_alc_select", "lagp_knn",
+            "lagp_mle_step", "lagp_predict", "lagp_predict_grad", "launch_count", "library",
+            "set_tuning")
+
+__all__ = list(_BINDING)
+
+
+def __getattr__(name):
+    if name in _BINDING:
+        from . import lagp
+        return getattr(lagp, name)
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

@@ -21,9 +21,8 @@
 // FP32 maximum, at most rescore_max, best first, ties to the lower row) ->
 // FP64 re-score of the contenders with Eq. (dxy) using FP64 K_j^{-1} ->
 // argmax (ties to the lower row) -> FP64 partitioned-inverse update of
-// K_j^{-1} (Sec. 2.2) -> FP32 recurrence with pivot x*.  The FP64 values of
-// the winner (its m_j^{-1} and k_j(x)^T K^{-1} k_j(x*)) also give lambda and
-// r_{x*} for the FP32 recurrence.
+// K_j^{-1} (Sec. 2.2) -> FP32 recurrence with pivot x*, whose lambda and
+// r_{x*} come from the pivot's own FP32 state (self-consistent factor).
 //
 // Layout: one persistent CTA per location at a time (atomic work counter);
 // candidate c lives in thread c / CPT, register slot c % CPT (v, r, score);
@@ -41,6 +40,15 @@ namespace {
 constexpr int F32_THREADS = 256;
 constexpr int F32_WARPS = F32_THREADS / 32;
 constexpr int LIST_CAP = 256;  // contender list capacity
+// Adaptive contender margin: FP32 scores within `margin` (relative) of the
+// FP32 maximum are re-scored in FP64, margin = min(rescore_rel,
+// max(MARGIN_MIN, MARGIN_KAPPA * err)), where err is the largest relative
+// FP32-vs-FP64 score error seen among the contenders re-scored so far,
+// decaying by ERR_DECAY per step (starting at ERR_INIT).
+constexpr float MARGIN_MIN = 0.02f;
+constexpr float MARGIN_KAPPA = 8.0f;
+constexpr float ERR_DECAY = 0.75f;
+constexpr float ERR_INIT = 0.05f;
 
 template <int JQ>
 __device__ __forceinline__ void contract64(const double *__restrict__ kc_s, const double *Kinv, int ld,
@@ -137,6 +145,7 @@ alc_f32_kernel(F32Params P) {
     float *xs32 = ustar + ld;                                  // p
     float *list_s = xs32 + p;                                  // LIST_CAP scores
     int *list_c = reinterpret_cast<int *>(list_s + LIST_CAP);  // LIST_CAP slots
+    int *list_r = list_c + LIST_CAP;                           // LIST_CAP design rows
 
     __shared__ int s_loc, s_bad, s_ncon, s_win;
     __shared__ int w_cnt[F32_WARPS];
@@ -144,7 +153,8 @@ alc_f32_kernel(F32Params P) {
     __shared__ int w_brow[F32_WARPS];
     __shared__ int con_slot[32], con_row[32];
     __shared__ double con_delta[32], con_minv[32], con_kxb[32], con_kap[32];
-    __shared__ float s_inv_lam, s_wnew, s_fmax;
+    __shared__ float s_vstar, s_covstar, s_fmax, s_err;
+    __shared__ float con_s32[32];
 
     float *U = P.U_ws + (size_t)blockIdx.x * nmax * Npad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -192,10 +202,12 @@ alc_f32_kernel(F32Params P) {
         const float inv_d = (float)(1.0 / d);
         const float gf = fmaxf((float)g, FLT_MIN);
         float v[CPT], cov[CPT], score[CPT];
+        int rows[CPT];  // design rows of this thread's candidates (tie-break key)
         unsigned chosen = 0;
 #pragma unroll
         for (int r = 0; r < CPT; r++) {
             const int c = c0 + r;
+            rows[r] = c < k ? cands[c] : INT32_MAX;
             float s = 0.f;
             for (int i = 0; i < p; i++) {
                 float df = coords[i * Npad + c] - (float)xq[i];
@@ -208,6 +220,7 @@ alc_f32_kernel(F32Params P) {
         }
 
         int status = LAGP_OK;
+        if (tid == 0) s_err = ERR_INIT;
         for (int j = 0; j < nm; j++) {
             // ---------------- contenders for design index j
             if (j < a.n0) {
@@ -223,10 +236,9 @@ alc_f32_kernel(F32Params P) {
 #pragma unroll
                 for (int r = 0; r < CPT; r++)
                     if (!(chosen >> r & 1u)) {
-                        int row = cands[c0 + r];
-                        if (score[r] > bm || (score[r] == bm && row < brow)) {
+                        if (score[r] > bm || (score[r] == bm && rows[r] < brow)) {
                             bm = score[r];
-                            brow = row;
+                            brow = rows[r];
                         }
                     }
 #pragma unroll
@@ -249,8 +261,9 @@ alc_f32_kernel(F32Params P) {
                     s_fmax = m0;
                 }
                 __syncthreads();
-                // contenders: FP32 score >= (1 - rel) * max, gathered in slot order
-                const float thr = s_fmax - P.rel * fabsf(s_fmax);
+                // contenders: FP32 score >= (1 - margin) * max, gathered in slot order
+                const float margin = fminf(P.rel, fmaxf(MARGIN_MIN, MARGIN_KAPPA * s_err));
+                const float thr = s_fmax - margin * fabsf(s_fmax);
                 unsigned flags = 0;
 #pragma unroll
                 for (int r = 0; r < CPT; r++)
@@ -276,6 +289,7 @@ alc_f32_kernel(F32Params P) {
                         if (pos < LIST_CAP) {
                             list_s[pos] = score[r];
                             list_c[pos] = c0 + r;
+                            list_r[pos] = rows[r];
                         }
                         pos++;
                     }
@@ -288,9 +302,8 @@ alc_f32_kernel(F32Params P) {
                         float bs = -FLT_MAX;
                         int brw = INT32_MAX, bpos = -1;
                         for (int e = lane; e < cnt; e += 32) {
-                            int c = list_c[e];
-                            if (c < 0) continue;
-                            int row = cands[c];
+                            if (list_c[e] < 0) continue;
+                            const int row = list_r[e];
                             if (list_s[e] > bs || (list_s[e] == bs && row < brw)) {
                                 bs = list_s[e];
                                 brw = row;
@@ -312,6 +325,7 @@ alc_f32_kernel(F32Params P) {
                         if (lane == 0) {
                             con_slot[ncon] = list_c[bpos];
                             con_row[ncon] = brw;
+                            con_s32[ncon] = bs;
                             list_c[bpos] = -1;
                         }
                         __syncwarp();
@@ -372,17 +386,15 @@ alc_f32_kernel(F32Params P) {
             __syncthreads();
             if (tid == 0) {
                 int wb = 0;
-                for (int w = 1; w < ncon; w++)
-                    if (better(con_delta[w], con_row[w], con_delta[wb], con_row[wb])) wb = w;
-                s_win = wb;
-                const double minv = con_minv[wb];
-                if (!(minv > 0.0)) {
-                    s_bad = LAGP_ENOTPD;
-                } else {
-                    const double lam = sqrt(minv);
-                    s_inv_lam = (float)(1.0 / lam);
-                    s_wnew = (float)((con_kap[wb] - con_kxb[wb]) / lam);
+                float e = 0.f;
+                for (int w = 0; w < ncon; w++) {
+                    if (w > 0 && better(con_delta[w], con_row[w], con_delta[wb], con_row[wb])) wb = w;
+                    if (j >= a.n0 && con_delta[w] > 0.0)
+                        e = fmaxf(e, (float)fabs((double)con_s32[w] / con_delta[w] - 1.0));
                 }
+                if (j >= a.n0) s_err = fmaxf(ERR_DECAY * s_err, e);
+                s_win = wb;
+                if (!(con_minv[wb] > 0.0)) s_bad = LAGP_ENOTPD;
             }
             __syncthreads();
             if (s_bad != LAGP_OK) {
@@ -394,9 +406,15 @@ alc_f32_kernel(F32Params P) {
             {
                 const double mu = 1.0 / con_minv[wb];
                 const double *b = con_b + (size_t)wb * ld;
-                for (int e = tid; e < j * j; e += F32_THREADS) {
-                    int r = e / j, c = e - r * j;
-                    Kinv[(size_t)r * ld + c] = fma(mu * b[r], b[c], Kinv[(size_t)r * ld + c]);
+                // lower triangle with its mirror: j(j+1)/2 FMAs
+                for (int e = tid; e < j * (j + 1) / 2; e += F32_THREADS) {
+                    int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+                    while ((r + 1) * (r + 2) / 2 <= e) r++;
+                    while (r * (r + 1) / 2 > e) r--;
+                    const int c = e - r * (r + 1) / 2;
+                    const double val = fma(mu * b[r], b[c], Kinv[(size_t)r * ld + c]);
+                    Kinv[(size_t)r * ld + c] = val;
+                    Kinv[(size_t)c * ld + r] = val;
                 }
                 for (int t = tid; t < j; t += F32_THREADS) {
                     double gt = -mu * b[t];
@@ -415,12 +433,23 @@ alc_f32_kernel(F32Params P) {
                 }
                 for (int i = tid; i < j; i += F32_THREADS) ustar[i] = U[(size_t)i * Npad + cstar];
             }
-            if (cstar >= c0 && cstar < c0 + CPT) chosen |= 1u << (cstar - c0);
+            // The FP32 recurrence continues from the pivot's own FP32 state:
+            // lambda^2 = v_{x*} and r_{x*}, so that U stays the Cholesky factor
+            // of one (slightly perturbed) matrix; mixing in the FP64 values
+            // breaks that consistency and the recurrence drifts.
+#pragma unroll
+            for (int r = 0; r < CPT; r++)
+                if (c0 + r == cstar) {
+                    s_vstar = v[r];
+                    s_covstar = cov[r];
+                    chosen |= 1u << r;
+                }
             __syncthreads();
             if (j + 1 >= nm) break;
             // ---------------- FP32 Schur recurrence with pivot x* (new column j of U)
             {
-                const float inv_lam = s_inv_lam, wnew = s_wnew;
+                const float inv_lam = rsqrtf(fmaxf(s_vstar, gf));
+                const float wnew = s_covstar * inv_lam;
                 float acc[CPT];
 #pragma unroll
                 for (int r = 0; r < CPT; r++) acc[r] = 0.f;
@@ -486,7 +515,7 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     const size_t ld = (size_t)((a.nmax + 31) & ~31);
     size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 + (size_t)a.nmax * a.p * 8 + (size_t)a.p * 8 +
                   (size_t)tmax * ld * 8 * 2 + (size_t)tmax * a.p * 8 + (size_t)a.p * Npad * 4 + ld * 4 +
-                  (size_t)a.p * 4 + (size_t)LIST_CAP * 8 + 64;
+                  (size_t)a.p * 4 + (size_t)LIST_CAP * 12 + 64;
     if (smem > ctx->smem_optin)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, N', p too large)");
     cudaFuncSetAttribute(alc_f32_kernel<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -29,7 +29,7 @@ struct lagp_ctx {
     void *ws[WS_NSLOTS] = {};
     size_t ws_bytes[WS_NSLOTS] = {};
     std::string err;
-    lagp_tuning tuning = {0, 0, 8, 0.05};
+    lagp_tuning tuning = {0, 0, 8, 0.5};
     int64_t launches = 0;
 };
 
