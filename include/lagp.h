@@ -206,6 +206,28 @@ lagp_status lagp_predict_grad(lagp_ctx *ctx, const void *X, const void *Y, int64
                               double *ds2_dd, double *ds2_dg, double *dllik_dd,
                               double *dllik_dg, int32_t *status);
 
+/* ----------------------------------------- a7 without device allocation
+ * The paper has no counterpart to this entry point.  It computes exactly what
+ * lagp_predict computes, for callers that cannot allocate device memory:
+ * applications whose own allocator owns all device memory after start-up,
+ * services under a device-memory budget fixed when they start, and
+ * latency-critical paths that cannot afford cudaMalloc's implicit device
+ * synchronisation.  Its scratch is a fixed array inside the library (2 MiB
+ * plus 256 bytes of device memory, held by every GPU that loads the library
+ * until the process exits), so the call itself calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *   Arguments, outputs and per-location status are those of lagp_predict.
+ *   Limit: n_max <= 64 (LAGP_EINVAL with an explanatory message otherwise).
+ *   All calls share the scratch: calls that overlap on the GPU (different
+ *   streams, or different contexts on one device) race, so order them.
+ *   The first call on a device looks up the scratch's device address, with
+ *   that device current; make this first call before any stream capture. */
+lagp_status lagp_predict_noalloc(lagp_ctx *ctx, const void *X, const void *Y, int64_t N,
+                                 int32_t p, lagp_dtype dtype, const void *Xref, int64_t M,
+                                 const int32_t *sel, const int32_t *n, int32_t n_max,
+                                 const double *d, double g, double *mean, double *s2, double *df,
+                                 int32_t *status);
+
 /* --------------------------------------------- whole method, host buffers
  * The multi-stage algorithm of Fig. 1 for every reference location:
  * kNN (a1) -> greedy ALC design at lengthscale d0 (a2..a6) -> optional local

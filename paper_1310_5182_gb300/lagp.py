@@ -60,6 +60,7 @@ def _load():
     lib.lagp_alc_select.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, I32, P, I32, P,
                                     D, ctypes.c_int, P, P, P]
     lib.lagp_predict.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P, P, P]
+    lib.lagp_predict_noalloc.argtypes = lib.lagp_predict.argtypes
     lib.lagp_mle_step.argtypes = [P, P, P, I64, I32, ctypes.c_int, I64, P, P, I32, P, D, D, D, I32,
                                   P, P, P, P, P]
     lib.lagp_predict_grad.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P,
@@ -67,7 +68,8 @@ def _load():
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
-              "lagp_knn", "lagp_alc_select", "lagp_predict", "lagp_mle_step", "lagp_predict_grad",
+              "lagp_knn", "lagp_alc_select", "lagp_predict", "lagp_predict_noalloc", "lagp_mle_step",
+              "lagp_predict_grad",
               "lagp_agp"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
@@ -233,6 +235,30 @@ def lagp_predict(X, Y, Xref, sel, n, d, g):
                                  _dev(out["s2"], "s2"), _dev(out["df"], "df"), _dev(status, "status")),
                ctx, "lagp_predict")
     out["status"] = status
+    return out
+
+
+def lagp_predict_noalloc(X, Y, Xref, sel, n, d, g, out=None):
+    """a7 through the entry point that allocates no device memory (scratch in
+    a fixed 2 MiB array inside the library; n_max <= 64).  For callers that
+    cannot allocate, pass preallocated `out` = dict(mean, s2, df (float64 [M])
+    and status (int32 [M])) and an int32 `n` / float64 `d` tensor of length M,
+    so that this wrapper allocates nothing either."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, n_max = sel.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    dt = d if (isinstance(d, torch.Tensor) and d.dtype == torch.float64 and d.is_cuda
+               and d.numel() == M and d.is_contiguous()) else _per_loc_f64(d, M, X.device)
+    if out is None:
+        out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in ("mean", "s2", "df")}
+        out["status"] = torch.empty(M, dtype=torch.int32, device=X.device)
+    _check(_lib.lagp_predict_noalloc(ctx, _dev(X, "X"), _dev(Y, "Y", X.dtype), N, p, _dtype_code(X),
+                                     _dev(Xref, "Xref", X.dtype), M, _dev(sel, "sel", torch.int32),
+                                     npp, n_max, _dev(dt, "d"), float(g), _dev(out["mean"], "mean"),
+                                     _dev(out["s2"], "s2"), _dev(out["df"], "df"),
+                                     _dev(out["status"], "status")),
+           ctx, "lagp_predict_noalloc")
     return out
 
 
