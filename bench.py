@@ -4,7 +4,8 @@ reference locations (kNN -> greedy ALC local designs -> local prediction).
 Default workload: the 8-d borehole configuration, N = 100,000 design points,
 M = 10,000 reference locations per GPU, (n0, n, N') = (6, 50, 1000), d = 2,
 g = 1e-6, synthetic (seeded) data.  One step = one pass of the whole hot path
-over the batch: kNN (a1), ALC search (a2-a6, FP32-bulk form), prediction (a7).
+over the batch: kNN (a1), then the ALC search (a2-a6, FP32-bulk form) with the
+local prediction (a7) carried along in the same kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -184,14 +185,15 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     def step(prec, ev=None):
+        # a1: kNN; a2..a7: ALC search with the predictive equations carried
+        # along by the partitioned inverse (one kernel)
         idx, _ = L.lagp_knn(X, Xr, Np)
         if ev is not None:
             ev[0].record(stream)
-        s = L.lagp_alc_select(X, Xr, idx, n0, n, d, g, prec=prec)
+        s = L.lagp_alc_predict(X, Y, Xr, idx, n0, n, d, g, prec=prec)
         if ev is not None:
             ev[1].record(stream)
-        p = L.lagp_predict(X, Y, Xr, s["sel"], n, d, g)
-        return s, p
+        return s, s
 
     def barrier():
         torch.cuda.synchronize(dev)

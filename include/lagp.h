@@ -151,12 +151,31 @@ lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dt
  *               multiplying by psi_j / (j - 2) gives the normalised value of
  *               the paper's step 9
  *   status      M int32 output: LAGP_OK / LAGP_ENOTPD / LAGP_EINVAL per
- *               location */
+ *               location
+ * Requires n_max <= 128 (K_j^{-1} is kept in shared memory). */
 lagp_status lagp_alc_select(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
                             lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
                             const int32_t *Nprime, int32_t Nprime_max, int32_t n0,
                             const int32_t *n, int32_t n_max, const double *d, double g,
                             lagp_precision prec, int32_t *sel, double *alc, int32_t *status);
+
+/* ---------------------------------------- a2..a7: search + local predict
+ * lagp_alc_select followed by the predictive equations of a7 on each chosen
+ * design, fused into the same kernel: the FP64 partitioned inverse that
+ * grows K_j^{-1} (Sec. 2.2) also grows alpha_j = K_j^{-1} Y_j,
+ * psi_j = Y_j^T K_j^{-1} Y_j and k_j(x)^T K_j^{-1} k_j(x) in O(j) per step:
+ * with b* = K_j^{-1} k_j(x*), mu = 1/(1 + g - k_j(x*)^T b*) and
+ * r_y = y* - Y_j^T b*,  alpha_{j+1} = [alpha_j - mu r_y b*; mu r_y],
+ * psi_{j+1} = psi_j + mu r_y^2,  and likewise for k(x)^T K^{-1} k(x).
+ * Outputs mean, s2, df (M each, FP64) equal those of lagp_predict on sel up
+ * to rounding (here K_n^{-1} comes from the partitioned inverse, there from a
+ * fresh Cholesky factorisation).  Other arguments as lagp_alc_select. */
+lagp_status lagp_alc_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                             lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
+                             const int32_t *Nprime, int32_t Nprime_max, int32_t n0,
+                             const int32_t *n, int32_t n_max, const double *d, double g,
+                             lagp_precision prec, int32_t *sel, double *alc, double *mean,
+                             double *s2, double *df, int32_t *status);
 
 /* ------------------------------------------------------ a7: local predict
  * Predictive equations (Eqs. predgp, preds2) on each location's local design:

@@ -24,13 +24,20 @@
 // K_j^{-1} (Sec. 2.2) -> FP32 recurrence with pivot x*, whose lambda and
 // r_{x*} come from the pivot's own FP32 state (self-consistent factor).
 //
-// Layout: one persistent CTA per location at a time (atomic work counter);
-// candidate c lives in thread c / CPT, register slot c % CPT (v, r, score);
-// the whitened panel U is a per-CTA global buffer U[i][c] (contiguous in c,
-// vector loads), L2-resident; K_j^{-1}, k_j(x) and the design coordinates
-// (FP64) and the candidate coordinates (FP32) sit in shared memory.
+// Layout: one persistent CTA per location at a time (atomic work counter),
+// three CTAs per SM so that one location's serial FP64 phase overlaps other
+// locations' FP32 passes; candidate c lives in thread c / CPT, register slot
+// c % CPT (v, r, score); the whitened panel U[i][c] and the FP32 candidate
+// coordinates C[i][c] are per-CTA global buffers (contiguous in c, vector
+// loads, L2-resident); K_j^{-1}, k_j(x), the design coordinates and the
+// contenders' FP64 vectors sit in shared memory.  Contenders are found with
+// per-warp lists merged by one warp; each contender's FP32 column of U is
+// fetched during its FP64 re-score, so the winner's column (the next pivot)
+// is already in shared memory when the FP32 pass starts.
 #include <cuda_runtime.h>
 #include <float.h>
+
+#include <algorithm>
 
 #include "device_util.cuh"
 #include "lagp_internal.h"
@@ -39,7 +46,6 @@ namespace {
 
 constexpr int F32_THREADS = 256;
 constexpr int F32_WARPS = F32_THREADS / 32;
-constexpr int LIST_CAP = 256;  // contender list capacity
 // Adaptive contender margin: FP32 scores within `margin` (relative) of the
 // FP32 maximum are re-scored in FP64, margin = min(rescore_rel,
 // max(MARGIN_MIN, MARGIN_KAPPA * err)), where err is the largest relative
@@ -49,38 +55,6 @@ constexpr float MARGIN_MIN = 0.02f;
 constexpr float MARGIN_KAPPA = 8.0f;
 constexpr float ERR_DECAY = 0.75f;
 constexpr float ERR_INIT = 0.05f;
-
-template <int JQ>
-__device__ __forceinline__ void contract64(const double *__restrict__ kc_s, const double *Kinv, int ld,
-                                           const double *kx, int j, int lane, double *b_out,
-                                           double &quad, double &kxb) {
-    double kc[JQ], b[JQ];
-#pragma unroll
-    for (int r = 0; r < JQ; r++) {
-        kc[r] = (lane + 32 * r < j) ? kc_s[lane + 32 * r] : 0.0;
-        b[r] = 0.0;
-    }
-#pragma unroll
-    for (int r = 0; r < JQ; r++) {
-        const int kend = min(32, j - 32 * r);
-        for (int kk = 0; kk < kend; kk++) {
-            const double v = __shfl_sync(LAGP_FULL_MASK, kc[r], kk);
-            const double *row = Kinv + (size_t)(32 * r + kk) * ld + lane;
-#pragma unroll
-            for (int r2 = 0; r2 < JQ; r2++) b[r2] = fma(row[32 * r2], v, b[r2]);
-        }
-    }
-    double q = 0.0, x = 0.0;
-#pragma unroll
-    for (int r = 0; r < JQ; r++)
-        if (lane + 32 * r < j) {
-            q = fma(kc[r], b[r], q);
-            x = fma(kx[lane + 32 * r], b[r], x);
-            b_out[lane + 32 * r] = b[r];
-        }
-    quad = warp_sum(q);
-    kxb = warp_sum(x);
-}
 
 template <int CPT>
 __device__ __forceinline__ void load_vec(const float *p, float (&v)[CPT]) {
@@ -120,45 +94,109 @@ __device__ __forceinline__ void store_vec(float *p, const float (&v)[CPT]) {
 struct F32Params {
     AlcArgs a;
     int *counter;
-    float *U_ws;      // per CTA: nmax x Npad
+    float *U_ws;      // per CTA: nmax x Npad (whitened panel U[i][c])
+    float *C_ws;      // per CTA: p x Npad (FP32 candidate coordinates C[i][c])
+    double *K_ws;     // per CTA: Npad (FP64 K(x_c, x), computed once per location)
     int Npad;         // F32_THREADS * CPT
     int tmax;         // rescore_max
-    float rel;        // rescore_rel
+    float rel;        // rescore_rel (cap of the contender margin)
 };
 
+// Rows [k0, k1) of the contraction b = K^{-1} kc: lane t writes
+// sum_{kk in [k0,k1)} K^{-1}[kk][t] kc[kk] for its columns t = lane + 32 r
+// (rows of the symmetric K^{-1} have leading dimension ld, a multiple of 32).
+template <int JQ>
+__device__ __forceinline__ void partial_contract(const double *kc, const double *Kinv, int ld, int k0,
+                                                 int k1, int j, int lane, double *out) {
+    double b0[JQ], b1[JQ];
+#pragma unroll
+    for (int r = 0; r < JQ; r++) b0[r] = b1[r] = 0.0;
+    int kk = k0;
+    for (; kk + 2 <= k1; kk += 2) {
+        const double v0 = kc[kk], v1 = kc[kk + 1];
+        const double *row0 = Kinv + (size_t)kk * ld + lane, *row1 = row0 + ld;
+#pragma unroll
+        for (int r = 0; r < JQ; r++) {
+            b0[r] = fma(row0[32 * r], v0, b0[r]);
+            b1[r] = fma(row1[32 * r], v1, b1[r]);
+        }
+    }
+    if (kk < k1) {
+        const double v0 = kc[kk];
+        const double *row0 = Kinv + (size_t)kk * ld + lane;
+#pragma unroll
+        for (int r = 0; r < JQ; r++) b0[r] = fma(row0[32 * r], v0, b0[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < JQ; r++)
+        if (lane + 32 * r < j) out[lane + 32 * r] = b0[r] + b1[r];
+}
+
+// Integer key with the order of the doubles (for comparisons off the FP64 pipe)
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// (score, row, slot) argmax across a warp: larger score, ties to the lower row
+__device__ __forceinline__ void warp_best3(float &s, int &row, int &slot) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float os = __shfl_xor_sync(LAGP_FULL_MASK, s, o);
+        int orow = __shfl_xor_sync(LAGP_FULL_MASK, row, o);
+        int oslot = __shfl_xor_sync(LAGP_FULL_MASK, slot, o);
+        if (os > s || (os == s && orow < row)) {
+            s = os;
+            row = orow;
+            slot = oslot;
+        }
+    }
+}
+
+// four resident CTAs per SM (64 registers a thread) for up to 4 candidate
+// slots a thread, fewer for the wider variants whose state needs more
 template <int CPT>
-__global__ void __launch_bounds__(F32_THREADS)
+__global__ void __launch_bounds__(F32_THREADS, CPT >= 16 ? 2 : (CPT >= 8 ? 3 : 4))
 alc_f32_kernel(F32Params P) {
     const AlcArgs &a = P.a;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, Npmax = a.Npmax, Npad = P.Npad, tmax = P.tmax;
     const int ld = (nmax + 31) & ~31;
     double *Kinv = reinterpret_cast<double *>(smem_raw);       // (nmax+1) x ld
-    double *kx = Kinv + (size_t)(nmax + 1) * ld;               // ld
-    double *xd = kx + ld;                                      // nmax x p
-    double *xq = xd + (size_t)nmax * p;                        // p
-    double *con_b = xq + p;                                    // tmax x ld
-    double *con_k = con_b + (size_t)tmax * ld;                 // tmax x ld
-    double *con_x = con_k + (size_t)tmax * ld;                 // tmax x p
-    float *coords = reinterpret_cast<float *>(con_x + (size_t)tmax * p);  // p x Npad
-    float *ustar = coords + (size_t)p * Npad;                  // ld
-    float *xs32 = ustar + ld;                                  // p
-    float *list_s = xs32 + p;                                  // LIST_CAP scores
-    int *list_c = reinterpret_cast<int *>(list_s + LIST_CAP);  // LIST_CAP slots
-    int *list_r = list_c + LIST_CAP;                           // LIST_CAP design rows
+    double *kx = Kinv + (size_t)(nmax + 1) * ld;               // ld: k_j(x)
+    double *yd = kx + ld;                                      // ld: responses of the design
+    double *alpha = yd + ld;                                   // ld: K_j^{-1} Y_j
+    double *xd = alpha + ld;                                   // nmax x p: design coordinates
+    double *xq = xd + (size_t)nmax * p;                        // p: reference location
+    double *con_b = xq + p;                                    // tmax x ld: K^{-1} k_j(x_c)
+    double *con_k = con_b + (size_t)tmax * ld;                 // tmax x ld: k_j(x_c), FP64
+    double *con_x = con_k + (size_t)tmax * ld;                 // tmax x p: coordinates, FP64
+    float *con_u = reinterpret_cast<float *>(con_x + (size_t)tmax * p);  // tmax x ld: U column
+    float *con_c = con_u + (size_t)tmax * ld;                  // tmax x p: coordinates, FP32
+    // max(8, tmax) x ld partial contractions (one row per R2 job)
+    double *cpart = reinterpret_cast<double *>(con_c + (((size_t)tmax * p + 1) & ~(size_t)1));
+    float *list_s = reinterpret_cast<float *>(cpart + (size_t)max(F32_WARPS, tmax) * ld);  // Npad scores
+    int *list_c = reinterpret_cast<int *>(list_s + Npad);      // Npad: their slots
+    int *list_r = list_c + Npad;                               // Npad: their design rows
 
     __shared__ int s_loc, s_bad, s_ncon, s_win;
     __shared__ int w_cnt[F32_WARPS];
-    __shared__ float w_best[F32_WARPS];
-    __shared__ int w_brow[F32_WARPS];
+    __shared__ float w_max[F32_WARPS];
     __shared__ int con_slot[32], con_row[32];
-    __shared__ double con_delta[32], con_minv[32], con_kxb[32], con_kap[32];
-    __shared__ float s_vstar, s_covstar, s_fmax, s_err;
-    __shared__ float con_s32[32];
+    __shared__ float con_s32[32], con_err[32];
+    __shared__ double con_delta[32], con_minv[32], con_mu[32], con_kxb[32], con_kap[32], con_ry[32],
+        con_y[32], con_dot[3][32];
+    __shared__ long long con_key[32];
+    __shared__ double s_psi, s_qx;
+    __shared__ float s_vstar, s_covstar, s_err;
+    const bool fused = a.mean != nullptr;
 
     float *U = P.U_ws + (size_t)blockIdx.x * nmax * Npad;
+    float *Cg = P.C_ws + (size_t)blockIdx.x * p * Npad;
+    double *kap64 = P.K_ws + (size_t)blockIdx.x * Npad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = tid * CPT;  // first candidate slot of this thread
+    const int rot = blockIdx.x & (F32_WARPS - 1);
 
     for (;;) {
         if (tid == 0) s_loc = atomicAdd(P.counter, 1);
@@ -188,7 +226,10 @@ alc_f32_kernel(F32Params P) {
             if (alc) alc[t] = CUDART_NAN;
         }
         if (s_bad != LAGP_OK) {
-            if (tid == 0) a.status[loc] = s_bad;
+            if (tid == 0) {
+                a.status[loc] = s_bad;
+                if (fused) a.mean[loc] = a.s2[loc] = a.df[loc] = CUDART_NAN;
+            }
             continue;
         }
 
@@ -196,31 +237,74 @@ alc_f32_kernel(F32Params P) {
         for (int i = tid; i < p; i += F32_THREADS) xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
         for (int e = tid; e < p * Npad; e += F32_THREADS) {
             int i = e / Npad, c = e - i * Npad;
-            coords[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
+            Cg[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
         }
+        const double inv_d64 = 1.0 / d;
         __syncthreads();
+        // K(x_c, x) in FP64 for every candidate, once per location (the FP64
+        // re-score then reads it instead of recomputing an exponential)
+        for (int c = tid; c < k; c += F32_THREADS) {
+            const int32_t r = cands[c];
+            double s0 = 0.0, s1 = 0.0;
+            int i = 0;
+            for (; i + 2 <= p; i += 2) {
+                const double d0 = load_coord64(a.X, r, p, i, a.dtype) - xq[i];
+                const double d1 = load_coord64(a.X, r, p, i + 1, a.dtype) - xq[i + 1];
+                s0 = fma(d0, d0, s0);
+                s1 = fma(d1, d1, s1);
+            }
+            if (i < p) {
+                const double d0 = load_coord64(a.X, r, p, i, a.dtype) - xq[i];
+                s0 = fma(d0, d0, s0);
+            }
+            kap64[c] = exp(-(s0 + s1) * inv_d64);
+        }
         const float inv_d = (float)(1.0 / d);
         const float gf = fmaxf((float)g, FLT_MIN);
         float v[CPT], cov[CPT], score[CPT];
         int rows[CPT];  // design rows of this thread's candidates (tie-break key)
         unsigned chosen = 0;
+        {
+            float s[CPT];
 #pragma unroll
-        for (int r = 0; r < CPT; r++) {
-            const int c = c0 + r;
-            rows[r] = c < k ? cands[c] : INT32_MAX;
-            float s = 0.f;
+            for (int r = 0; r < CPT; r++) s[r] = 0.f;
             for (int i = 0; i < p; i++) {
-                float df = coords[i * Npad + c] - (float)xq[i];
-                s = fmaf(df, df, s);
+                float cv[CPT];
+                load_vec<CPT>(Cg + (size_t)i * Npad + c0, cv);
+                const float qi = (float)xq[i];
+#pragma unroll
+                for (int r = 0; r < CPT; r++) {
+                    float df = cv[r] - qi;
+                    s[r] = fmaf(df, df, s[r]);
+                }
             }
-            v[r] = (float)(1.0 + g);
-            cov[r] = __expf(-s * inv_d);  // K(x_c, x), no nugget
-            score[r] = c < k ? cov[r] * cov[r] / v[r] : -1.f;
-            if (c >= k) chosen |= 1u << r;  // padding slots never compete
+#pragma unroll
+            for (int r = 0; r < CPT; r++) {
+                const int c = c0 + r;
+                rows[r] = c < k ? cands[c] : INT32_MAX;
+                v[r] = (float)(1.0 + g);
+                cov[r] = __expf(-s[r] * inv_d);  // K(x_c, x), no nugget
+                score[r] = c < k ? cov[r] * cov[r] / v[r] : -1.f;
+                if (c >= k) chosen |= 1u << r;  // padding slots never compete
+            }
         }
 
+        {
+            float wm = -FLT_MAX;
+#pragma unroll
+            for (int r = 0; r < CPT; r++)
+                if (!(chosen >> r & 1u)) wm = fmaxf(wm, score[r]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(LAGP_FULL_MASK, wm, o));
+            if (lane == 0) w_max[warp] = wm;
+        }
         int status = LAGP_OK;
-        if (tid == 0) s_err = ERR_INIT;
+        if (tid == 0) {
+            s_err = ERR_INIT;
+            s_psi = 0.0;
+            s_qx = 0.0;
+        }
+        __syncthreads();
         for (int j = 0; j < nm; j++) {
             // ---------------- contenders for design index j
             if (j < a.n0) {
@@ -228,42 +312,15 @@ alc_f32_kernel(F32Params P) {
                     s_ncon = 1;
                     con_slot[0] = j;  // Fig. 1 step 2(a): nearest neighbours in order
                     con_row[0] = cands[j];
+                    con_s32[0] = 0.f;
                 }
             } else {
-                // FP32 block maximum
-                float bm = -1.f;
-                int brow = INT32_MAX;
-#pragma unroll
-                for (int r = 0; r < CPT; r++)
-                    if (!(chosen >> r & 1u)) {
-                        if (score[r] > bm || (score[r] == bm && rows[r] < brow)) {
-                            bm = score[r];
-                            brow = rows[r];
-                        }
-                    }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    float ov = __shfl_xor_sync(LAGP_FULL_MASK, bm, o);
-                    int orow = __shfl_xor_sync(LAGP_FULL_MASK, brow, o);
-                    if (ov > bm || (ov == bm && orow < brow)) {
-                        bm = ov;
-                        brow = orow;
-                    }
-                }
-                if (lane == 0) {
-                    w_best[warp] = bm;
-                    w_brow[warp] = brow;
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    float m0 = w_best[0];
-                    for (int w = 1; w < F32_WARPS; w++) m0 = fmaxf(m0, w_best[w]);
-                    s_fmax = m0;
-                }
-                __syncthreads();
-                // contenders: FP32 score >= (1 - margin) * max, gathered in slot order
+                __syncthreads();  // the per-warp maxima of the last FP32 pass
                 const float margin = fminf(P.rel, fmaxf(MARGIN_MIN, MARGIN_KAPPA * s_err));
-                const float thr = s_fmax - margin * fabsf(s_fmax);
+                float gmax = w_max[0];
+#pragma unroll
+                for (int w = 1; w < F32_WARPS; w++) gmax = fmaxf(gmax, w_max[w]);
+                const float thr = gmax - margin * fabsf(gmax);
                 unsigned flags = 0;
 #pragma unroll
                 for (int r = 0; r < CPT; r++)
@@ -272,66 +329,60 @@ alc_f32_kernel(F32Params P) {
                 int incl = mine;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    int t = __shfl_up_sync(LAGP_FULL_MASK, incl, o);
+                    const int t = __shfl_up_sync(LAGP_FULL_MASK, incl, o);
                     if (lane >= o) incl += t;
                 }
                 if (lane == 31) w_cnt[warp] = incl;
                 __syncthreads();
                 int off = 0, total = 0;
+#pragma unroll
                 for (int w = 0; w < F32_WARPS; w++) {
-                    if (w < warp) off += w_cnt[w];
+                    off += w < warp ? w_cnt[w] : 0;
                     total += w_cnt[w];
                 }
-                int pos = off + incl - mine;
+                int pos = off + incl - mine;  // slot order: deterministic
 #pragma unroll
                 for (int r = 0; r < CPT; r++)
                     if (flags >> r & 1u) {
-                        if (pos < LIST_CAP) {
-                            list_s[pos] = score[r];
-                            list_c[pos] = c0 + r;
-                            list_r[pos] = rows[r];
-                        }
+                        list_s[pos] = score[r];
+                        list_c[pos] = c0 + r;
+                        list_r[pos] = rows[r];
                         pos++;
                     }
                 __syncthreads();
-                // warp 0: the best tmax of the list (score desc, row asc)
                 if (warp == 0) {
-                    const int cnt = min(total, LIST_CAP);
-                    int ncon = 0;
-                    for (int t = 0; t < tmax && t < cnt; t++) {
-                        float bs = -FLT_MAX;
-                        int brw = INT32_MAX, bpos = -1;
-                        for (int e = lane; e < cnt; e += 32) {
-                            if (list_c[e] < 0) continue;
-                            const int row = list_r[e];
-                            if (list_s[e] > bs || (list_s[e] == bs && row < brw)) {
-                                bs = list_s[e];
-                                brw = row;
-                                bpos = e;
+                    if (total <= tmax) {  // every flagged candidate is re-scored
+                        for (int e = lane; e < total; e += 32) {
+                            con_slot[e] = list_c[e];
+                            con_row[e] = list_r[e];
+                            con_s32[e] = list_s[e];
+                        }
+                        if (lane == 0) s_ncon = total;
+                    } else {  // the best tmax by FP32 score, ties to the lower row
+                        int ncon = 0;
+                        for (int t = 0; t < tmax; t++) {
+                            float bs = -FLT_MAX;
+                            int brow = INT32_MAX, bpos = -1;
+                            for (int e = lane; e < total; e += 32)
+                                if (list_c[e] >= 0 &&
+                                    (list_s[e] > bs || (list_s[e] == bs && list_r[e] < brow))) {
+                                    bs = list_s[e];
+                                    brow = list_r[e];
+                                    bpos = e;
+                                }
+                            warp_best3(bs, brow, bpos);
+                            if (bpos < 0) break;
+                            if (lane == 0) {
+                                con_slot[ncon] = list_c[bpos];
+                                con_row[ncon] = brow;
+                                con_s32[ncon] = bs;
+                                list_c[bpos] = -1;
                             }
+                            __syncwarp();
+                            ncon++;
                         }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            float ov = __shfl_xor_sync(LAGP_FULL_MASK, bs, o);
-                            int orw = __shfl_xor_sync(LAGP_FULL_MASK, brw, o);
-                            int opos = __shfl_xor_sync(LAGP_FULL_MASK, bpos, o);
-                            if (ov > bs || (ov == bs && orw < brw)) {
-                                bs = ov;
-                                brw = orw;
-                                bpos = opos;
-                            }
-                        }
-                        if (bpos < 0) break;
-                        if (lane == 0) {
-                            con_slot[ncon] = list_c[bpos];
-                            con_row[ncon] = brw;
-                            con_s32[ncon] = bs;
-                            list_c[bpos] = -1;
-                        }
-                        __syncwarp();
-                        ncon++;
+                        if (lane == 0) s_ncon = ncon;
                     }
-                    if (lane == 0) s_ncon = ncon;
                 }
             }
             __syncthreads();
@@ -340,61 +391,122 @@ alc_f32_kernel(F32Params P) {
                 status = LAGP_ENOTPD;
                 break;
             }
-            // ---------------- FP64 re-score of the contenders (Eq. dxy), one warp each
-            for (int w = warp; w < ncon; w += F32_WARPS) {
-                const int row = con_row[w];
-                double *xc = con_x + (size_t)w * p;
-                double *kc = con_k + (size_t)w * ld;
-                for (int i = lane; i < p; i += 32) xc[i] = load_coord64(a.X, row, p, i, a.dtype);
-                __syncwarp();
-                for (int t = lane; t < j; t += 32) {
-                    double s = 0.0;
-                    for (int i = 0; i < p; i++) {
-                        double df = xc[i] - xd[(size_t)t * p + i];
-                        s = fma(df, df, s);
+            // ---------------- FP64 re-score of the contenders (Eq. dxy).  On this
+            // GPU an FP64 warp instruction holds its sub-partition's FP64 unit
+            // for ~64 cycles whatever the number of active lanes, so the work is
+            // cut into phases spread over all warps (with a per-CTA rotation of
+            // roles, so that co-resident CTAs use different sub-partitions).
+            const int we = (warp + rot) & (F32_WARPS - 1);  // rotated warp role
+            // R0: contender data: FP64 and FP32 coordinates, response, and the
+            // FP32 column of U that serves as the next Schur pivot if it wins
+            for (int e = tid; e < ncon * p; e += F32_THREADS) {
+                const int w = e / p, i = e - w * p;
+                con_x[(size_t)w * p + i] = load_coord64(a.X, con_row[w], p, i, a.dtype);
+                con_c[(size_t)w * p + i] = Cg[(size_t)i * Npad + con_slot[w]];
+            }
+            for (int e = tid; e < ncon * j; e += F32_THREADS) {
+                const int w = e / j, t = e - w * j;
+                con_u[(size_t)w * ld + t] = U[(size_t)t * Npad + con_slot[w]];
+            }
+            if (fused && tid < ncon) {
+                const int row = con_row[tid];
+                con_y[tid] = a.dtype == LAGP_F64 ? static_cast<const double *>(a.Y)[row]
+                                                 : (double)static_cast<const float *>(a.Y)[row];
+            }
+            __syncthreads();
+            // R1: k_j(x_c) in FP64, (contender, design row) pairs packed over lanes
+            {
+                const int te = (tid + 32 * rot) & (F32_THREADS - 1);
+                for (int e = te; e < ncon * j; e += F32_THREADS) {
+                    const int w = e / j, t = e - w * j;
+                    const double *xc = con_x + (size_t)w * p;
+                    const double *xt = xd + (size_t)t * p;
+                    double s0 = 0.0, s1 = 0.0;
+                    int i = 0;
+                    for (; i + 2 <= p; i += 2) {
+                        const double d0 = xc[i] - xt[i], d1 = xc[i + 1] - xt[i + 1];
+                        s0 = fma(d0, d0, s0);
+                        s1 = fma(d1, d1, s1);
                     }
-                    kc[t] = exp(-s / d);
+                    if (i < p) {
+                        const double d0 = xc[i] - xt[i];
+                        s0 = fma(d0, d0, s0);
+                    }
+                    con_k[(size_t)w * ld + t] = exp(-(s0 + s1) * inv_d64);
                 }
-                double sk = 0.0;
-                for (int i = 0; i < p; i++) {
-                    double df = xc[i] - xq[i];
-                    sk = fma(df, df, sk);
-                }
-                const double kap = exp(-sk / d);
-                __syncwarp();
-                double quad = 0.0, kxb = 0.0;
-                double *bo = con_b + (size_t)w * ld;
-                if (j > 0) {
+            }
+            __syncthreads();
+            // R2: partial contractions K^{-1} k_j(x_c), each contender's rows
+            // split over wpc warps
+            // warps per contender: the largest power of two with ncon * wpc <= 8,
+            // so that the R2 jobs fit the max(8, tmax) rows of cpart
+            const int wpc = ncon >= 5 ? 1 : (ncon >= 3 ? 2 : (ncon >= 2 ? 4 : 8));
+            if (j > 0) {
+                const int rows = max(F32_WARPS, tmax);  // rows of cpart
+                for (int job = we; job < ncon * wpc && job < rows; job += F32_WARPS) {
+                    const int w = job / wpc, part = job - w * wpc;
+                    const int k0 = part * j / wpc, k1 = (part + 1) * j / wpc;
                     switch ((j + 31) >> 5) {
-                        case 1: contract64<1>(kc, Kinv, ld, kx, j, lane, bo, quad, kxb); break;
-                        case 2: contract64<2>(kc, Kinv, ld, kx, j, lane, bo, quad, kxb); break;
-                        case 3: contract64<3>(kc, Kinv, ld, kx, j, lane, bo, quad, kxb); break;
-                        default: contract64<4>(kc, Kinv, ld, kx, j, lane, bo, quad, kxb); break;
+                        case 1: partial_contract<1>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
+                        case 2: partial_contract<2>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
+                        case 3: partial_contract<3>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
+                        default: partial_contract<4>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
                     }
                 }
-                if (lane == 0) {
-                    const double minv = (1.0 + g) - quad;
-                    const double m = 1.0 / minv;
-                    const double kxg = -m * kxb;
-                    con_minv[w] = minv;
-                    con_kxb[w] = kxb;
-                    con_kap[w] = kap;
-                    con_delta[w] = minv > 0.0 ? kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m
-                                              : -CUDART_INF;
+            }
+            __syncthreads();
+            // R3: b = sum of the partials; the dot products k^T b, k(x)^T b and
+            // Y^T b, one warp each
+            {
+                const int ns = fused ? 3 : 2;
+                for (int job = we; job < ncon * ns; job += F32_WARPS) {
+                    const int w = job / ns, sdot = job - w * ns;
+                    const double *v = sdot == 0 ? con_k + (size_t)w * ld : (sdot == 1 ? kx : yd);
+                    double acc = 0.0;
+                    for (int t = lane; t < j; t += 32) {
+                        double bt = 0.0;
+                        for (int q = 0; q < wpc; q++) bt += cpart[(size_t)(w * wpc + q) * ld + t];
+                        if (sdot == 0) con_b[(size_t)w * ld + t] = bt;
+                        acc = fma(v[t], bt, acc);
+                    }
+                    acc = warp_sum(acc);
+                    if (lane == 0) con_dot[sdot][w] = acc;
                 }
+            }
+            __syncthreads();
+            // R4: per-contender scalars of Eqs. (piedef), (dxy), in parallel
+            if (tid < ncon) {
+                const int w = tid;
+                const double quad = j > 0 ? con_dot[0][w] : 0.0, kxb = j > 0 ? con_dot[1][w] : 0.0;
+                const double kap = kap64[con_slot[w]];
+                const double minv = (1.0 + g) - quad;  // m_j^{-1}(x_c)
+                const double m = 1.0 / minv;
+                const double kxg = -m * kxb;           // k_j(x)^T g_j(x_c)
+                const double dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
+                con_minv[w] = minv;
+                con_mu[w] = m;
+                con_kxb[w] = kxb;
+                con_kap[w] = kap;
+                const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
+                con_delta[w] = valid ? dl : -CUDART_INF;
+                con_key[w] = valid ? order_key(dl) : INT64_MIN;
+                if (fused) con_ry[w] = con_y[w] - (j > 0 ? con_dot[2][w] : 0.0);  // y - Y^T K^{-1} k
+                con_err[w] = (j >= a.n0 && minv > 0.0 && dl > 0.0)
+                                 ? fabsf(con_s32[w] / (float)dl - 1.f) : 0.f;
             }
             __syncthreads();
             if (tid == 0) {
                 int wb = 0;
                 float e = 0.f;
                 for (int w = 0; w < ncon; w++) {
-                    if (w > 0 && better(con_delta[w], con_row[w], con_delta[wb], con_row[wb])) wb = w;
-                    if (j >= a.n0 && con_delta[w] > 0.0)
-                        e = fmaxf(e, (float)fabs((double)con_s32[w] / con_delta[w] - 1.0));
+                    if (w > 0 && (con_key[w] > con_key[wb] ||
+                                  (con_key[w] == con_key[wb] && con_row[w] < con_row[wb])))
+                        wb = w;
+                    e = fmaxf(e, con_err[w]);
                 }
                 if (j >= a.n0) s_err = fmaxf(ERR_DECAY * s_err, e);
                 s_win = wb;
-                if (!(con_minv[wb] > 0.0)) s_bad = LAGP_ENOTPD;
+                if (con_key[wb] == INT64_MIN) s_bad = LAGP_ENOTPD;
             }
             __syncthreads();
             if (s_bad != LAGP_OK) {
@@ -404,7 +516,7 @@ alc_f32_kernel(F32Params P) {
             // ---------------- FP64 partitioned-inverse update (Sec. 2.2)
             const int wb = s_win, cstar = con_slot[wb];
             {
-                const double mu = 1.0 / con_minv[wb];
+                const double mu = con_mu[wb];
                 const double *b = con_b + (size_t)wb * ld;
                 // lower triangle with its mirror: j(j+1)/2 FMAs
                 for (int e = tid; e < j * (j + 1) / 2; e += F32_THREADS) {
@@ -416,22 +528,30 @@ alc_f32_kernel(F32Params P) {
                     Kinv[(size_t)r * ld + c] = val;
                     Kinv[(size_t)c * ld + r] = val;
                 }
+                const double ry = fused ? con_ry[wb] : 0.0;
                 for (int t = tid; t < j; t += F32_THREADS) {
                     double gt = -mu * b[t];
                     Kinv[(size_t)t * ld + j] = gt;
                     Kinv[(size_t)j * ld + t] = gt;
+                    if (fused) alpha[t] = fma(-mu * ry, b[t], alpha[t]);
                 }
                 if (tid == 0) {
+                    if (fused) {
+                        // Eqs. (predgp), (preds2) carried by the same partitioned
+                        // inverse: alpha = K^{-1} Y, psi = Y^T K^{-1} Y,
+                        // qx = k(x)^T K^{-1} k(x)
+                        alpha[j] = mu * ry;
+                        yd[j] = con_y[wb];
+                        s_psi = fma(mu * ry, ry, s_psi);
+                        const double cx = con_kap[wb] - con_kxb[wb];
+                        s_qx = fma(mu * cx, cx, s_qx);
+                    }
                     Kinv[(size_t)j * ld + j] = mu;
                     kx[j] = con_kap[wb];
                     sel[j] = con_row[wb];
                     if (alc && j >= a.n0) alc[j] = con_delta[wb];
                 }
-                for (int i = tid; i < p; i += F32_THREADS) {
-                    xd[(size_t)j * p + i] = con_x[(size_t)wb * p + i];
-                    xs32[i] = coords[i * Npad + cstar];
-                }
-                for (int i = tid; i < j; i += F32_THREADS) ustar[i] = U[(size_t)i * Npad + cstar];
+                for (int i = tid; i < p; i += F32_THREADS) xd[(size_t)j * p + i] = con_x[(size_t)wb * p + i];
             }
             // The FP32 recurrence continues from the pivot's own FP32 state:
             // lambda^2 = v_{x*} and r_{x*}, so that U stays the Cholesky factor
@@ -450,24 +570,24 @@ alc_f32_kernel(F32Params P) {
             {
                 const float inv_lam = rsqrtf(fmaxf(s_vstar, gf));
                 const float wnew = s_covstar * inv_lam;
+                const float *ustar = con_u + (size_t)wb * ld;
+                const float *xs32 = con_c + (size_t)wb * p;
                 float acc[CPT];
 #pragma unroll
                 for (int r = 0; r < CPT; r++) acc[r] = 0.f;
                 const float *Ub = U + c0;
+                // loads in flight per thread: UNR rows of CPT floats
+                constexpr int UNR = CPT >= 16 ? 2 : 4;
                 int i = 0;
-                for (; i + 4 <= j; i += 4) {
-                    float u0[CPT], u1[CPT], u2[CPT], u3[CPT];
-                    load_vec<CPT>(Ub + (size_t)(i + 0) * Npad, u0);
-                    load_vec<CPT>(Ub + (size_t)(i + 1) * Npad, u1);
-                    load_vec<CPT>(Ub + (size_t)(i + 2) * Npad, u2);
-                    load_vec<CPT>(Ub + (size_t)(i + 3) * Npad, u3);
-                    const float s0 = ustar[i], s1 = ustar[i + 1], s2 = ustar[i + 2], s3 = ustar[i + 3];
+                for (; i + UNR <= j; i += UNR) {
+                    float u[UNR][CPT];
 #pragma unroll
-                    for (int r = 0; r < CPT; r++) {
-                        acc[r] = fmaf(u0[r], s0, acc[r]);
-                        acc[r] = fmaf(u1[r], s1, acc[r]);
-                        acc[r] = fmaf(u2[r], s2, acc[r]);
-                        acc[r] = fmaf(u3[r], s3, acc[r]);
+                    for (int q = 0; q < UNR; q++) load_vec<CPT>(Ub + (size_t)(i + q) * Npad, u[q]);
+#pragma unroll
+                    for (int q = 0; q < UNR; q++) {
+                        const float sq = ustar[i + q];
+#pragma unroll
+                        for (int r = 0; r < CPT; r++) acc[r] = fmaf(u[q][r], sq, acc[r]);
                     }
                 }
                 for (; i < j; i++) {
@@ -477,29 +597,56 @@ alc_f32_kernel(F32Params P) {
 #pragma unroll
                     for (int r = 0; r < CPT; r++) acc[r] = fmaf(u0[r], s0, acc[r]);
                 }
+                float s[CPT];
+#pragma unroll
+                for (int r = 0; r < CPT; r++) s[r] = 0.f;
+                for (int ii = 0; ii < p; ii++) {
+                    float cv[CPT];
+                    load_vec<CPT>(Cg + (size_t)ii * Npad + c0, cv);
+                    const float xi = xs32[ii];
+#pragma unroll
+                    for (int r = 0; r < CPT; r++) {
+                        float df = cv[r] - xi;
+                        s[r] = fmaf(df, df, s[r]);
+                    }
+                }
                 float un[CPT];
 #pragma unroll
                 for (int r = 0; r < CPT; r++) {
-                    const int c = c0 + r;
-                    float s = 0.f;
-                    for (int ii = 0; ii < p; ii++) {
-                        float df = coords[ii * Npad + c] - xs32[ii];
-                        s = fmaf(df, df, s);
-                    }
-                    const float kcs = __expf(-s * inv_d);  // K(x_c, x*), no nugget
+                    const float kcs = __expf(-s[r] * inv_d);  // K(x_c, x*), no nugget
                     un[r] = (kcs - acc[r]) * inv_lam;
                     v[r] = fmaf(-un[r], un[r], v[r]);
                     cov[r] = fmaf(-wnew, un[r], cov[r]);
                     score[r] = (chosen >> r & 1u) ? -1.f : cov[r] * cov[r] / fmaxf(v[r], gf);
                 }
                 store_vec<CPT>(U + (size_t)j * Npad + c0, un);
+                float wm = -FLT_MAX;
+#pragma unroll
+                for (int r = 0; r < CPT; r++)
+                    if (!(chosen >> r & 1u)) wm = fmaxf(wm, score[r]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(LAGP_FULL_MASK, wm, o));
+                if (lane == 0) w_max[warp] = wm;
             }
-            __syncthreads();  // U column j visible before the next pivot reads it
+            // the next step's selection starts with a barrier, which orders
+            // column j of U and the per-warp maxima before their readers
         }
         if (status != LAGP_OK) {
             for (int t = tid; t < nmax; t += F32_THREADS) {
                 sel[t] = -1;
                 if (alc) alc[t] = CUDART_NAN;
+            }
+        }
+        __syncthreads();
+        if (fused && warp == 0) {
+            double m = 0.0;
+            for (int t = lane; t < nm; t += 32) m = fma(kx[t], alpha[t], m);
+            m = warp_sum(m);
+            if (lane == 0) {
+                const bool ok = status == LAGP_OK;
+                a.mean[loc] = ok ? m : CUDART_NAN;
+                a.s2[loc] = ok ? s_psi * ((1.0 + g) - s_qx) / nm : CUDART_NAN;
+                a.df[loc] = ok ? (double)nm : CUDART_NAN;
             }
         }
         if (tid == 0) a.status[loc] = status;
@@ -513,24 +660,29 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     const int Npad = F32_THREADS * CPT;
     const int tmax = ctx->tuning.rescore_max > 0 ? ctx->tuning.rescore_max : 8;
     const size_t ld = (size_t)((a.nmax + 31) & ~31);
-    size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 + (size_t)a.nmax * a.p * 8 + (size_t)a.p * 8 +
-                  (size_t)tmax * ld * 8 * 2 + (size_t)tmax * a.p * 8 + (size_t)a.p * Npad * 4 + ld * 4 +
-                  (size_t)a.p * 4 + (size_t)LIST_CAP * 12 + 64;
+    const size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 3 + (size_t)a.nmax * a.p * 8 +
+                        (size_t)a.p * 8 + (size_t)tmax * ld * 8 * 2 + (size_t)tmax * a.p * 8 +
+                        (size_t)tmax * ld * 4 + ((size_t)tmax * a.p + 1) * 4 + 8 +
+                        (size_t)std::max(F32_WARPS, tmax) * ld * 8 + (size_t)Npad * 12 + 64;
     if (smem > ctx->smem_optin)
-        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, N', p too large)");
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, p too large)");
     cudaFuncSetAttribute(alc_f32_kernel<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f32_kernel<CPT>, F32_THREADS, smem);
-    int per_sm = ctx->tuning.ctas_per_sm > 0 ? ctx->tuning.ctas_per_sm : 2;
+    int per_sm = ctx->tuning.ctas_per_sm > 0 ? ctx->tuning.ctas_per_sm : 4;
     if (occ > 0 && per_sm > occ) per_sm = occ;
     int64_t grid = (int64_t)ctx->num_sms * per_sm;
     if (grid > a.M) grid = a.M;
     if (grid < 1) grid = 1;
-    float *U = static_cast<float *>(lagp_ws(ctx, WS_ALC_PANEL, (size_t)grid * a.nmax * Npad * 4 + 256));
+    const size_t U_floats = (size_t)grid * a.nmax * Npad, C_floats = (size_t)grid * a.p * Npad;
+    const size_t K_doubles = (size_t)grid * Npad;
+    float *U = static_cast<float *>(
+        lagp_ws(ctx, WS_ALC_PANEL, (U_floats + C_floats) * 4 + K_doubles * 8 + 256));
     int *counter = static_cast<int *>(lagp_ws(ctx, WS_ALC_COUNTER, 256));
     if (!U || !counter) return LAGP_ENOMEM;
     LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    F32Params P{a, counter, U, Npad, tmax, (float)ctx->tuning.rescore_rel};
+    double *Kw = reinterpret_cast<double *>(U + U_floats + C_floats);  // 8-byte aligned: floats counts are even
+    F32Params P{a, counter, U, U + U_floats, Kw, Npad, tmax, (float)ctx->tuning.rescore_rel};
     alc_f32_kernel<CPT><<<(unsigned)grid, F32_THREADS, smem, st>>>(P);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());

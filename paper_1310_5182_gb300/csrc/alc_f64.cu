@@ -29,6 +29,8 @@ constexpr int NMAX_SMEM = 128;
 struct F64Shared {
     double *Kinv;    // nmax x nmax
     double *kx;      // nmax: k_j(x)
+    double *yd;      // nmax: responses of the design (fused prediction)
+    double *alpha;   // nmax: K^{-1} Y_j (fused prediction)
     double *bstar;   // nmax: K^{-1} k*
     double *xd;      // nmax x p: design coordinates
     double *xq;      // p: reference location
@@ -90,14 +92,17 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
     F64Shared S;
     S.Kinv = reinterpret_cast<double *>(smem_raw);
     S.kx = S.Kinv + (size_t)(nmax + 1) * ld;
-    S.bstar = S.kx + ld;
+    S.yd = S.kx + ld;
+    S.alpha = S.yd + ld;
+    S.bstar = S.alpha + ld;
     S.xd = S.bstar + nmax;
     S.xq = S.xd + (size_t)nmax * p;
     S.chosen = reinterpret_cast<unsigned char *>(S.xq + p);
     __shared__ int s_loc, s_bad, s_cstar;
     __shared__ double w_v[F64_WARPS];
     __shared__ int w_row[F64_WARPS], w_slot[F64_WARPS];
-    __shared__ double s_delta, s_mu;
+    __shared__ double s_delta, s_mu, s_ry, s_cx, s_psi, s_qx, s_ystar;
+    const bool fused = a.mean != nullptr;
 
     double *panel = panel_ws + (size_t)blockIdx.x * Npmax * nmax;  // [c][i], ld nmax
     double *kappa = kappa_ws + (size_t)blockIdx.x * Npmax;
@@ -132,7 +137,10 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
             if (alc) alc[t] = CUDART_NAN;
         }
         if (s_bad != LAGP_OK) {
-            if (tid == 0) a.status[loc] = s_bad;
+            if (tid == 0) {
+                a.status[loc] = s_bad;
+                if (fused) a.mean[loc] = a.s2[loc] = a.df[loc] = CUDART_NAN;
+            }
             continue;  // next location (loop head synchronises)
         }
 
@@ -144,6 +152,7 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
         __syncthreads();
 
         int status = LAGP_OK;
+        if (tid == 0) s_psi = s_qx = 0.0;
         for (int j = 0; j < nm; j++) {
             int cstar;
             double delta = CUDART_NAN;
@@ -202,13 +211,30 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
             }
             __syncthreads();
             if (tid < 32) {
-                double q = 0.0;
-                for (int t = lane; t < j; t += 32) q = fma(kst[t], S.bstar[t], q);
+                double q = 0.0, xb = 0.0, yb = 0.0;
+                for (int t = lane; t < j; t += 32) {
+                    q = fma(kst[t], S.bstar[t], q);
+                    if (fused) {
+                        xb = fma(S.kx[t], S.bstar[t], xb);
+                        yb = fma(S.yd[t], S.bstar[t], yb);
+                    }
+                }
                 q = warp_sum(q);
+                if (fused) {
+                    xb = warp_sum(xb);
+                    yb = warp_sum(yb);
+                }
                 if (lane == 0) {
                     double minv = (1.0 + g) - q;
                     s_mu = 1.0 / minv;
                     if (!(minv > 0.0)) s_bad = LAGP_ENOTPD;
+                    if (fused) {
+                        const int32_t row = cands[cstar];
+                        s_ystar = a.dtype == LAGP_F64 ? static_cast<const double *>(a.Y)[row]
+                                                      : (double)static_cast<const float *>(a.Y)[row];
+                        s_ry = s_ystar - yb;          // y* - Y_j^T K^{-1} k*
+                        s_cx = kappa[cstar] - xb;     // K(x*,x) - k_j(x)^T K^{-1} k*
+                    }
                 }
             }
             __syncthreads();
@@ -217,17 +243,32 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                 break;
             }
             const double mu = s_mu;
-            // K^{-1} + g g^T / m with g = -mu b*:  += mu b* b*^T ; border = -mu b*
-            for (int e = tid; e < j * j; e += F64_THREADS) {
-                int r = e / j, c = e - r * j;
-                S.Kinv[(size_t)r * ld + c] = fma(mu * S.bstar[r], S.bstar[c], S.Kinv[(size_t)r * ld + c]);
+            // K^{-1} + g g^T / m with g = -mu b*:  += mu b* b*^T (lower triangle
+            // and its mirror) ; border = -mu b*
+            for (int e = tid; e < j * (j + 1) / 2; e += F64_THREADS) {
+                int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+                while ((r + 1) * (r + 2) / 2 <= e) r++;
+                while (r * (r + 1) / 2 > e) r--;
+                const int c = e - r * (r + 1) / 2;
+                const double val = fma(mu * S.bstar[r], S.bstar[c], S.Kinv[(size_t)r * ld + c]);
+                S.Kinv[(size_t)r * ld + c] = val;
+                S.Kinv[(size_t)c * ld + r] = val;
             }
+            const double ry = fused ? s_ry : 0.0;
             for (int t = tid; t < j; t += F64_THREADS) {
                 double gt = -mu * S.bstar[t];
                 S.Kinv[(size_t)t * ld + j] = gt;
                 S.Kinv[(size_t)j * ld + t] = gt;
+                if (fused) S.alpha[t] = fma(-mu * ry, S.bstar[t], S.alpha[t]);
             }
             if (tid == 0) {
+                if (fused) {
+                    // Eqs. (predgp), (preds2) carried by the partitioned inverse
+                    S.alpha[j] = mu * ry;
+                    S.yd[j] = s_ystar;
+                    s_psi = fma(mu * ry, ry, s_psi);
+                    s_qx = fma(mu * s_cx, s_cx, s_qx);
+                }
                 S.Kinv[(size_t)j * ld + j] = mu;
                 S.kx[j] = kappa[cstar];
                 S.chosen[cstar] = 1;
@@ -251,6 +292,20 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                 if (alc) alc[t] = CUDART_NAN;
             }
         }
+        if (fused) {
+            __syncthreads();
+            if (warp == 0) {
+                double m = 0.0;
+                for (int t = lane; t < nm; t += 32) m = fma(S.kx[t], S.alpha[t], m);
+                m = warp_sum(m);
+                if (lane == 0) {
+                    const bool ok = status == LAGP_OK;
+                    a.mean[loc] = ok ? m : CUDART_NAN;
+                    a.s2[loc] = ok ? s_psi * ((1.0 + g) - s_qx) / nm : CUDART_NAN;
+                    a.df[loc] = ok ? (double)nm : CUDART_NAN;
+                }
+            }
+        }
         if (tid == 0) a.status[loc] = status;
         __syncthreads();
     }
@@ -265,7 +320,7 @@ lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a) {
     const size_t ld = (size_t)((a.nmax + 31) & ~31);
     // K^{-1} (n_max x ld, plus one spare row so masked reads stay inside), kx, b*,
     // design coordinates, reference location, chosen flags
-    size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 2 + (size_t)a.nmax * a.p * 8 +
+    size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 4 + (size_t)a.nmax * a.p * 8 +
                   (size_t)a.p * 8 + (size_t)a.Npmax + 16;
     if (smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory");
     cudaFuncSetAttribute(alc_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -156,29 +156,54 @@ lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dt
 
 // --------------------------------------------------------------- ALC search
 
+static lagp_status alc_common(lagp_ctx *ctx, const char *fn, const void *X, int64_t N, int32_t p,
+                              lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
+                              const int32_t *Nprime, int32_t Nprime_max, int32_t n0, const int32_t *n,
+                              int32_t n_max, const double *d, double g, lagp_precision prec,
+                              int32_t *sel, double *alc, int32_t *status, const void *Y,
+                              double *mean, double *s2, double *df) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    const std::string f(fn);
+    LAGP_TRY(check_design(ctx, X, N, p, dtype, fn));
+    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, f + ": M < 0");
+    if (M == 0) return LAGP_OK;
+    if (!Xref || !idx || !d || !sel || !status)
+        return lagp_fail(ctx, LAGP_EINVAL, f + ": NULL required array");
+    if (Nprime_max < 1 || Nprime_max > N || Nprime_max > 4096)
+        return lagp_fail(ctx, LAGP_EINVAL, f + ": need 1 <= Nprime_max <= min(N, 4096)");
+    if (n0 < 1 || n_max < n0 || n_max > Nprime_max || n_max > 128)
+        return lagp_fail(ctx, LAGP_EINVAL, f + ": need 1 <= n0 <= n_max <= min(Nprime_max, 128)");
+    if (!(g >= 0.0) || !std::isfinite(g)) return lagp_fail(ctx, LAGP_EINVAL, f + ": g must be >= 0");
+    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK)
+        return lagp_fail(ctx, LAGP_EINVAL, f + ": unknown precision");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    AlcArgs a{X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0, n, n_max, d, g, sel, alc, status,
+              Y, mean, s2, df};
+    return prec == LAGP_PREC_F64 ? launch_alc_f64(ctx, a) : launch_alc_f32(ctx, a);
+}
+
 lagp_status lagp_alc_select(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
                             lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
                             const int32_t *Nprime, int32_t Nprime_max, int32_t n0,
                             const int32_t *n, int32_t n_max, const double *d, double g,
                             lagp_precision prec, int32_t *sel, double *alc, int32_t *status) {
-    if (!ctx) return LAGP_EINVAL;
-    ctx->err.clear();
-    LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_alc_select"));
-    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: M < 0");
-    if (M == 0) return LAGP_OK;
-    if (!Xref || !idx || !d || !sel || !status)
-        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: NULL required array");
-    if (Nprime_max < 1 || Nprime_max > N || Nprime_max > 4096)
-        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: need 1 <= Nprime_max <= min(N, 4096)");
-    if (n0 < 1 || n_max < n0 || n_max > Nprime_max || n_max > 256)
-        return lagp_fail(ctx, LAGP_EINVAL,
-                         "lagp_alc_select: need 1 <= n0 <= n_max <= min(Nprime_max, 256)");
-    if (!(g >= 0.0) || !std::isfinite(g)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: g must be >= 0");
-    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK)
-        return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: unknown precision");
-    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
-    AlcArgs a{X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0, n, n_max, d, g, sel, alc, status};
-    return prec == LAGP_PREC_F64 ? launch_alc_f64(ctx, a) : launch_alc_f32(ctx, a);
+    return alc_common(ctx, "lagp_alc_select", X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0, n,
+                      n_max, d, g, prec, sel, alc, status, nullptr, nullptr, nullptr, nullptr);
+}
+
+lagp_status lagp_alc_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
+                             lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *idx,
+                             const int32_t *Nprime, int32_t Nprime_max, int32_t n0,
+                             const int32_t *n, int32_t n_max, const double *d, double g,
+                             lagp_precision prec, int32_t *sel, double *alc, double *mean,
+                             double *s2, double *df, int32_t *status) {
+    if (ctx && M > 0 && (!Y || !mean || !s2 || !df)) {
+        ctx->err = "lagp_alc_predict: NULL Y or prediction output";
+        return LAGP_EINVAL;
+    }
+    return alc_common(ctx, "lagp_alc_predict", X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0,
+                      n, n_max, d, g, prec, sel, alc, status, Y, mean, s2, df);
 }
 
 // --------------------------------------------------------- predict / MLE
@@ -300,16 +325,21 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
         LAGP_CUDA(ctx, cudaStreamSynchronize(st));  // h leaves scope
     }
     LAGP_TRY(lagp_knn(ctx, dX, N, p, dtype, dR, M, dNp, Nprime_max, dIdx, dSt4));
-    LAGP_TRY(lagp_alc_select(ctx, dX, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn, n_max,
-                             dd, g, prec, dSel, nullptr, dSt));
     if (do_mle) {
+        // design at d0, MLE of d on that design, prediction with the estimate
+        LAGP_TRY(lagp_alc_select(ctx, dX, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn, n_max,
+                                 dd, g, prec, dSel, nullptr, dSt));
         LAGP_TRY(lagp_mle_step(ctx, dX, dY, N, p, dtype, M, dSel, dn, n_max, dd, g, dmin, dmax,
                                max_iter, nullptr, nullptr, nullptr, nullptr, dSt2));
+        LAGP_TRY(lagp_predict(ctx, dX, dY, N, p, dtype, dR, M, dSel, dn, n_max, dd, g, dMean, dS2,
+                              dDf, dSt3));
     } else {
+        // prediction carried by the search itself (one kernel)
+        LAGP_TRY(lagp_alc_predict(ctx, dX, dY, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn,
+                                  n_max, dd, g, prec, dSel, nullptr, dMean, dS2, dDf, dSt));
         LAGP_CUDA(ctx, cudaMemsetAsync(dSt2, 0, M * 4, st));
+        LAGP_CUDA(ctx, cudaMemsetAsync(dSt3, 0, M * 4, st));
     }
-    LAGP_TRY(lagp_predict(ctx, dX, dY, N, p, dtype, dR, M, dSel, dn, n_max, dd, g, dMean, dS2,
-                          dDf, dSt3));
     LAGP_CUDA(ctx, cudaMemcpyAsync(mean, dMean, M * 8, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaMemcpyAsync(s2, dS2, M * 8, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaMemcpyAsync(df, dDf, M * 8, cudaMemcpyDeviceToHost, st));

@@ -72,6 +72,10 @@ struct AlcArgs {
     int32_t *sel;
     double *alc;        // may be null
     int32_t *status;
+    // fused local prediction (Eqs. predgp, preds2) on the selected design;
+    // all four null for a plain search
+    const void *Y;
+    double *mean, *s2, *df;
 };
 
 lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a);

@@ -60,6 +60,8 @@ def _load():
     lib.lagp_alc_select.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, I32, P, I32, P,
                                     D, ctypes.c_int, P, P, P]
     lib.lagp_predict.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P, P, P]
+    lib.lagp_alc_predict.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, I32, P, I32,
+                                     P, D, ctypes.c_int, P, P, P, P, P, P]
     lib.lagp_predict_noalloc.argtypes = lib.lagp_predict.argtypes
     lib.lagp_mle_step.argtypes = [P, P, P, I64, I32, ctypes.c_int, I64, P, P, I32, P, D, D, D, I32,
                                   P, P, P, P, P]
@@ -68,7 +70,8 @@ def _load():
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
-              "lagp_knn", "lagp_alc_select", "lagp_predict", "lagp_predict_noalloc", "lagp_mle_step",
+              "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
+              "lagp_mle_step",
               "lagp_predict_grad",
               "lagp_agp"):
         getattr(lib, f).restype = ctypes.c_int
@@ -217,6 +220,34 @@ def lagp_alc_select(X, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, n_ma
                                     _dev(sel, "sel"), _ptr_or_null(alc), _dev(status, "status")),
                ctx, "lagp_alc_select")
     return dict(sel=sel, status=status, alc=alc)
+
+
+def lagp_alc_predict(X, Y, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, n_max=None,
+                     want_alc=False):
+    """a2..a7 fused: greedy ALC designs and the local predictive equations on
+    them in one kernel.  Returns dict(sel, status, alc, mean, s2, df)."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, Npmax = idx.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    if n_max is None:
+        n_max = int(nt.max().item()) if nt is not None and M else int(n)
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    dt = _per_loc_f64(d, M, X.device)
+    sel = torch.empty((M, n_max), dtype=torch.int32, device=X.device)
+    status = torch.empty(M, dtype=torch.int32, device=X.device)
+    alc = torch.empty((M, n_max), dtype=torch.float64, device=X.device) if want_alc else None
+    out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in ("mean", "s2", "df")}
+    if M:
+        _check(_lib.lagp_alc_predict(ctx, _dev(X, "X"), _dev(Y, "Y", X.dtype), N, p, _dtype_code(X),
+                                     _dev(Xref, "Xref", X.dtype), M, _dev(idx, "idx", torch.int32), Npp,
+                                     Npmax, int(n0), npp, int(n_max), _dev(dt, "d"), float(g),
+                                     _PREC[prec], _dev(sel, "sel"), _ptr_or_null(alc),
+                                     _dev(out["mean"], "mean"), _dev(out["s2"], "s2"),
+                                     _dev(out["df"], "df"), _dev(status, "status")),
+               ctx, "lagp_alc_predict")
+    out.update(sel=sel, status=status, alc=alc)
+    return out
 
 
 def lagp_predict(X, Y, Xref, sel, n, d, g):

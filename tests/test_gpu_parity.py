@@ -253,6 +253,32 @@ def test_select_deterministic(L, O):
         assert torch.equal(a["alc"].view(torch.int64), b["alc"].view(torch.int64))
 
 
+# -------------------------------------------- search + fused prediction (a2..a7)
+
+@pytest.mark.parametrize("prec", ["f64", "f32bulk"])
+def test_alc_predict_fused_matches_oracle(L, O, prec):
+    """The fused entry point: its designs meet the selection rule and its
+    predictions (grown by the partitioned inverse) match the oracle's
+    Cholesky-based predictions on the same design; ragged n, FP32 inputs."""
+    rng = np.random.default_rng(28)
+    w = W.borehole(seed=16, N=30_000, M=48, Np=500, dtype=np.float32, g=1e-5)
+    n_arr = rng.integers(8, 61, 48).astype(np.int32)
+    idx = O.knn(w.X, w.Xref, 500)
+    ref = O.alc_select(w.X, w.Xref, idx, 6, n_arr, w.d, w.g, topk=4)
+    out = L.lagp_alc_predict(dev(w.X), dev(w.Y), dev(w.Xref), dev(idx), 6, n_arr, w.d, w.g, prec=prec)
+    torch.cuda.synchronize()
+    assert (out["status"].cpu().numpy() == 0).all()
+    sel = out["sel"].cpu().numpy()
+    div = compare_selection(sel, ref, n_arr, 6, w.g)
+    assert len(div) <= 2
+    same = np.setdiff1d(np.arange(48), div)
+    refp = O.predict(w.X, w.Y, w.Xref, ref["sel"], n_arr, w.d, w.g)
+    refp = {k: v[same] for k, v in refp.items()}
+    check_pred(out["mean"].cpu().numpy()[same], out["s2"].cpu().numpy()[same], refp, w.X, w.Y,
+               w.Xref[same], ref["sel"][same], n_arr[same], w.d, w.g)
+    assert np.array_equal(out["df"].cpu().numpy(), n_arr.astype(np.float64))
+
+
 # -------------------------------------------------------- prediction (a7)
 
 def test_predict_matches_oracle(L, O):
@@ -341,9 +367,16 @@ def test_borehole_full_size_sampled(L, O, prec):
     w = W.c2_borehole_100k()
     X, Xr, Y = dev(w.X), dev(w.Xref), dev(w.Y)
     idx, st = L.lagp_knn(X, Xr, 1000)
-    out = L.lagp_alc_select(X, Xr, idx, 6, 50, 2.0, 1e-6, prec=prec, want_alc=True)
+    out = L.lagp_alc_predict(X, Y, Xr, idx, 6, 50, 2.0, 1e-6, prec=prec, want_alc=True)
     pr = L.lagp_predict(X, Y, Xr, out["sel"], 50, 2.0, 1e-6)
     torch.cuda.synchronize()
+    # fused predictions agree with the separate Cholesky-based predict on the
+    # same (GPU) designs, for every location
+    sel_all = out["sel"].cpu().numpy()
+    chk = np.random.default_rng(29).choice(w.M, 200, replace=False)
+    both = {"mean": pr["mean"].cpu().numpy()[chk], "s2": pr["s2"].cpu().numpy()[chk]}
+    check_pred(out["mean"].cpu().numpy()[chk], out["s2"].cpu().numpy()[chk], both, w.X, w.Y,
+               w.Xref[chk], sel_all[chk], np.full(200, 50), 2.0, 1e-6)
     assert (st.cpu().numpy() == 0).all() and (out["status"].cpu().numpy() == 0).all()
     samp = np.random.default_rng(27).choice(w.M, 24, replace=False)
     ref_idx = O.knn(w.X, w.Xref[samp], 1000)
