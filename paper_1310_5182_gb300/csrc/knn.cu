@@ -4,13 +4,17 @@
 // Design (GB300): distances are screened in FP32 (74 TFLOP/s) and only the
 // few candidates near the N'-th distance are re-ranked in FP64 (1.2 TFLOP/s).
 //   knn_prep    FP32 copy of an FP64 design, and R = max |coordinate|.
-//   knn_screen  one warp per query, eight queries per CTA sharing each design
-//               tile in shared memory; three passes over the design:
-//               (1) 2048-bin histogram of the FP32 distance bits [30:20],
-//               (2) 2048-bin histogram of bits [19:9] inside the boundary bin,
-//               giving tau >= the N'-th smallest FP32 distance,
-//               (3) collect every row whose FP32 distance is below tau widened
-//               by a rigorous FP32-vs-FP64 error margin (see screen_margin).
+//   knn_screen  persistent; 16 queries per CTA, two per warp, sharing every
+//               design tile in shared memory:
+//               (A, B) 2-level histogram (FP32 distance bits [30:21], then
+//               [20:11] inside the boundary bin) over a strided sample of the
+//               design, giving a threshold tau0 expected to bound about 1.3 N'
+//               rows (with stride 1, exactly the N'-th smallest distance);
+//               (C) one pass over the whole design collecting every row below
+//               tau0 widened by a rigorous FP32-vs-FP64 error margin (see
+//               screen_margin) and counting the rows below tau0.  A query
+//               whose count is short of N', or whose buffer overflowed, is
+//               redone by a second launch with stride 1 (the exact method).
 //   knn_sort    one CTA per query: exact FP64 distances of the collected rows
 //               (separately rounded subtract/multiply/add in coordinate order),
 //               bitonic sort on (d2, row), first N' rows written out.
@@ -25,10 +29,22 @@
 
 namespace {
 
-constexpr int QB = 8;                 // queries per CTA, one warp each
-constexpr int SCREEN_THREADS = QB * 32;
-constexpr int HB = 2048;              // histogram bins per level
-constexpr int TILE_FLOATS = 8192;     // shared floats for one design tile
+constexpr int QPW = 2;                // queries per warp
+constexpr int SCREEN_THREADS = 256;
+constexpr int QB = QPW * SCREEN_THREADS / 32;  // 16 queries per CTA
+constexpr int HB = 1024;              // histogram bins per level (10 bits)
+constexpr int L1_SHIFT = 21;          // level 1: FP32 distance bits [30:21]
+constexpr int L2_SHIFT = 11;          // level 2: bits [20:11] inside the boundary bin
+constexpr uint32_t L2_LOW = (1u << L2_SHIFT) - 1;
+constexpr int TILE_FLOATS = 4096;     // floats of one design tile (tile length x p)
+constexpr int STAGE = TILE_FLOATS / SCREEN_THREADS;  // floats a thread stages per tile
+
+// Design points per tile: a multiple of 32 with tile length x p <= TILE_FLOATS,
+// at most 512.
+__host__ __device__ inline int tile_len(int p) {
+    int t = (TILE_FLOATS / p) & ~31;
+    return t > 512 ? 512 : (t < 32 ? 32 : t);
+}
 constexpr int CAND_CAP = 8192;        // candidate capacity cap (sort in shared memory)
 constexpr int SORT_THREADS = 256;
 
@@ -105,107 +121,217 @@ __device__ void find_bin(const uint32_t *h, uint32_t target, int lane, uint32_t 
     }
 }
 
-// FP32 screen distance of design tile point t to the warp's query (held in
-// registers for the compile-time dimensions, in shared memory otherwise).
-template <int P>
-__device__ __forceinline__ float screen_d2(const float *tile, int stride, int t, const float (&qr)[P > 0 ? P : 1],
-                                           const float *qsm, int p) {
-    float s = 0.f;
-    if constexpr (P > 0) {
+// One design tile against a warp's QPW queries.  PASS 0: level-1 histogram;
+// PASS 1: level-2 histogram inside the boundary bin; PASS 2: collection.
+template <int P, int PASS>
+__device__ __forceinline__ void screen_tile(const float *t, int TS, int cnt, int lane, int p,
+                                            const float (&qr)[QPW][P > 0 ? P : 1],
+                                            const float *qsw, const bool (&ok)[QPW], uint32_t *histw,
+                                            const uint32_t (&b1)[QPW], const float (&tau0)[QPW],
+                                            const float (&tau2f)[QPW], int32_t *cntw, int32_t *cnt0w,
+                                            int32_t *__restrict__ cand, const int64_t (&q)[QPW],
+                                            int32_t Cmax, int64_t base) {
+    for (int pt = lane; pt < cnt; pt += 32) {
+        float sd[QPW] = {};
+        if constexpr (P > 0) {
 #pragma unroll
-        for (int i = 0; i < P; i++) {
-            float df = tile[t * stride + i] - qr[i];
-            s = fmaf(df, df, s);
+            for (int i = 0; i < P; i++) {
+                const float x = t[i * TS + pt];
+#pragma unroll
+                for (int h = 0; h < QPW; h++) {
+                    const float df = x - qr[h][i];
+                    sd[h] = fmaf(df, df, sd[h]);
+                }
+            }
+        } else {
+            for (int i = 0; i < p; i++) {
+                const float x = t[i * TS + pt];
+#pragma unroll
+                for (int h = 0; h < QPW; h++) {
+                    const float df = x - qsw[h * p + i];
+                    sd[h] = fmaf(df, df, sd[h]);
+                }
+            }
         }
-    } else {
-        for (int i = 0; i < p; i++) {
-            float df = tile[t * stride + i] - qsm[i];
-            s = fmaf(df, df, s);
+#pragma unroll
+        for (int h = 0; h < QPW; h++) {
+            if constexpr (PASS == 0) {
+                if (ok[h]) atomicAdd(&histw[h * HB + ((__float_as_uint(sd[h]) >> L1_SHIFT) & (HB - 1))], 1u);
+            } else if constexpr (PASS == 1) {
+                const uint32_t bits = __float_as_uint(sd[h]);
+                if (ok[h] && ((bits >> L1_SHIFT) & (HB - 1)) == b1[h])
+                    atomicAdd(&histw[h * HB + ((bits >> L2_SHIFT) & (HB - 1))], 1u);
+            } else {
+                if (ok[h] && sd[h] <= tau2f[h]) {
+                    if (sd[h] <= tau0[h]) atomicAdd(&cnt0w[h], 1);
+                    const int pos = atomicAdd(&cntw[h], 1);
+                    if (pos < Cmax) cand[q[h] * Cmax + pos] = (int32_t)(base + pt);
+                }
+            }
         }
     }
-    return s;
 }
 
+// Screen of one block of QB queries (two per warp) against the design.
+//   Passes A, B: 2-level histogram of the FP32 distances to the sampled rows
+//   r = 0, s, 2s, ...; the rtarget-th smallest sampled distance gives tau0
+//   (upper edge of its level-2 bin).  With s = 1 (small designs, and the exact
+//   retry) rtarget = N' and tau0 bounds the N'-th smallest FP32 distance.
+//   Pass C: every row whose FP32 distance is <= screen_margin(tau0) is
+//   collected, and the rows <= tau0 are counted; when that count reaches N'
+//   the collected set provably holds the exact FP64 top N' (see
+//   screen_margin).  Otherwise (a sample that underestimated the threshold)
+//   or when the buffer overflows, the query is flagged for the exact retry.
 template <int P>
 __global__ void __launch_bounds__(SCREEN_THREADS, 2)
 knn_screen(const float *__restrict__ X32, int64_t N, int p, const void *__restrict__ Xref,
            lagp_dtype dt, int64_t M, const int32_t *__restrict__ Np, int32_t Npmax,
            const unsigned long long *__restrict__ Rbits, int32_t *__restrict__ cand, int32_t Cmax,
-           int32_t *__restrict__ cand_count, int32_t *__restrict__ status) {
+           int32_t *__restrict__ cand_count, int32_t *__restrict__ status, int64_t stride,
+           int32_t *__restrict__ retry, int retry_pass, int *__restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);
-    float *tile = reinterpret_cast<float *>(hist + QB * HB);
-    float *qs = tile + TILE_FLOATS;
-    __shared__ int32_t s_count[QB];
-
+    const int TT = tile_len(p), TS = TT + 1;  // tile length and padded stride
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);   // QB x HB
+    float *tiles = reinterpret_cast<float *>(hist + QB * HB);  // 2 x p x TS
+    float *qs = tiles + 2 * (size_t)p * TS;                      // QB x p
+    __shared__ int32_t s_count[QB], s_count0[QB];
+    __shared__ int64_t s_blk;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t q = (int64_t)blockIdx.x * QB + w;
-    const bool active = q < M;
-    const int k = active ? (Np ? Np[q] : Npmax) : 0;
-    const bool ok = active && k >= 1 && k <= Npmax;
-    const int stride = p + 1;  // odd stride: conflict-free per-lane rows
-    int T = (TILE_FLOATS / stride) & ~31;
-    if (T > 1024) T = 1024;
-
-    float qreg[P > 0 ? P : 1] = {};
-    for (int i = lane; i < p; i += 32) qs[w * p + i] = active ? load_coord32(Xref, q, p, i, dt) : 0.f;
-    for (int b = lane; b < HB; b += 32) hist[w * HB + b] = 0;
-    if (lane == 0) s_count[w] = 0;
-    __syncthreads();
-    if constexpr (P > 0) {
-#pragma unroll
-        for (int i = 0; i < P; i++) qreg[i] = qs[w * p + i];
-    }
     const double R = __longlong_as_double((long long)*Rbits);
+    const int64_t nsamp = (N + stride - 1) / stride;
 
-    uint32_t b1 = 0, before = 0;
-    double tau2 = 0.0;
-    for (int pass = 0; pass < 3; pass++) {
-        for (int64_t base = 0; base < N; base += T) {
-            const int cnt = (int)min((int64_t)T, N - base);
-            __syncthreads();
-            const float *src = X32 + base * p;
-            for (int e = threadIdx.x; e < cnt * p; e += SCREEN_THREADS) {
-                int t = e / p, i = e - t * p;
-                tile[t * stride + i] = src[e];
-            }
-            __syncthreads();
-            if (ok) {
-                for (int t = lane; t < cnt; t += 32) {
-                    float s = screen_d2<P>(tile, stride, t, qreg, qs + w * p, p);
-                    uint32_t bits = __float_as_uint(s);
-                    uint32_t hi = (bits >> 20) & 0x7FFu;
-                    if (pass == 0) {
-                        atomicAdd(&hist[w * HB + hi], 1u);
-                    } else if (pass == 1) {
-                        if (hi == b1) atomicAdd(&hist[w * HB + ((bits >> 9) & 0x7FFu)], 1u);
-                    } else if ((double)s <= tau2) {
-                        int pos = atomicAdd(&s_count[w], 1);
-                        if (pos < Cmax) cand[q * Cmax + pos] = (int32_t)(base + t);
+    for (;;) {
+        if (threadIdx.x == 0) s_blk = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t blk = s_blk;
+        __syncthreads();
+        if (blk * QB >= M) break;
+
+        int64_t q[QPW];
+        int k[QPW], rtarget[QPW];
+        bool ok[QPW], active[QPW];
+        bool mine_any = false;
+#pragma unroll
+        for (int h = 0; h < QPW; h++) {
+            const int ql = w * QPW + h;
+            q[h] = blk * QB + ql;
+            active[h] = q[h] < M;
+            k[h] = active[h] ? (Np ? Np[q[h]] : Npmax) : 0;
+            ok[h] = active[h] && k[h] >= 1 && k[h] <= Npmax;
+            if (retry_pass) ok[h] = ok[h] && retry[q[h]] != 0;  // exact retry: flagged queries only
+            mine_any |= ok[h];
+            rtarget[h] = stride == 1 ? k[h]
+                                     : (int)min((int64_t)((13 * (int64_t)k[h] + 10 * stride - 1) / (10 * stride)) + 16, nsamp);
+            for (int i = lane; i < p; i += 32) qs[ql * p + i] = active[h] ? load_coord32(Xref, q[h], p, i, dt) : 0.f;
+            for (int b = lane; b < HB; b += 32) hist[ql * HB + b] = 0;
+            if (lane == 0) s_count[ql] = s_count0[ql] = 0;
+        }
+        if (!__syncthreads_or(mine_any)) continue;  // nothing to do in this block
+        float qr[QPW][P > 0 ? P : 1] = {};
+        if constexpr (P > 0) {
+#pragma unroll
+            for (int h = 0; h < QPW; h++)
+#pragma unroll
+                for (int i = 0; i < P; i++) qr[h][i] = qs[(w * QPW + h) * p + i];
+        }
+
+        uint32_t b1[QPW] = {}, before[QPW] = {};
+        // thresholds as floats: for a float distance s, s <= t (t real) holds
+        // exactly when s <= t rounded down to a float, so the hot loop compares
+        // in FP32 (an FP64 compare per point would occupy the slow FP64 unit)
+        float tau0[QPW] = {}, tau2f[QPW] = {};
+        for (int pass = 0; pass < 3; pass++) {
+            const int64_t rstride = pass < 2 ? stride : 1;  // passes A, B: sampled rows
+            const int64_t nrows = pass < 2 ? nsamp : N;
+            const int64_t ntiles = (nrows + TT - 1) / TT;
+            float stage[STAGE];
+            auto load_stage = [&](int64_t tile) {
+                const int64_t base = tile * TT;
+                const int cnt = (int)min((int64_t)TT, nrows - base);
+#pragma unroll
+                for (int u = 0; u < STAGE; u++) {
+                    const int e = threadIdx.x + u * SCREEN_THREADS;
+                    if (e < cnt * p) {
+                        const int pt = (P > 0) ? e / P : e / p, i = e - pt * p;
+                        stage[u] = X32[(base + pt) * rstride * p + i];
+                    } else {
+                        stage[u] = 0.f;
                     }
                 }
+            };
+            auto store_stage = [&](int buf) {
+                float *t = tiles + (size_t)buf * p * TS;
+#pragma unroll
+                for (int u = 0; u < STAGE; u++) {
+                    const int e = threadIdx.x + u * SCREEN_THREADS;
+                    if (e < TT * p) {
+                        const int pt = (P > 0) ? e / P : e / p, i = e - pt * p;
+                        t[i * TS + pt] = stage[u];
+                    }
+                }
+            };
+            load_stage(0);
+            store_stage(0);
+            __syncthreads();
+            for (int64_t tile = 0; tile < ntiles; tile++) {
+                const int buf = (int)(tile & 1);
+                if (tile + 1 < ntiles) load_stage(tile + 1);  // in flight during the screen
+                const int64_t base = tile * TT;
+                const int cnt = (int)min((int64_t)TT, nrows - base);
+                const float *t = tiles + (size_t)buf * p * TS;
+                if (pass == 0)
+                    screen_tile<P, 0>(t, TS, cnt, lane, p, qr, qs + w * QPW * p, ok, hist + w * QPW * HB,
+                                      b1, tau0, tau2f, s_count + w * QPW, s_count0 + w * QPW, cand, q,
+                                      Cmax, base);
+                else if (pass == 1)
+                    screen_tile<P, 1>(t, TS, cnt, lane, p, qr, qs + w * QPW * p, ok, hist + w * QPW * HB,
+                                      b1, tau0, tau2f, s_count + w * QPW, s_count0 + w * QPW, cand, q,
+                                      Cmax, base);
+                else
+                    screen_tile<P, 2>(t, TS, cnt, lane, p, qr, qs + w * QPW * p, ok, hist + w * QPW * HB,
+                                      b1, tau0, tau2f, s_count + w * QPW, s_count0 + w * QPW, cand, q,
+                                      Cmax, base);
+                __syncthreads();  // every warp is done with the other buffer
+                if (tile + 1 < ntiles) store_stage(buf ^ 1);
+                __syncthreads();
+            }
+#pragma unroll
+            for (int h = 0; h < QPW; h++) {
+                if (!ok[h]) continue;
+                uint32_t *hh = hist + (w * QPW + h) * HB;
+                if (pass == 0) {
+                    find_bin(hh, (uint32_t)rtarget[h], lane, b1[h], before[h]);
+                    __syncwarp();
+                    for (int b = lane; b < HB; b += 32) hh[b] = 0;
+                } else if (pass == 1) {
+                    uint32_t b2, before2;
+                    find_bin(hh, (uint32_t)rtarget[h] - before[h], lane, b2, before2);
+                    tau0[h] = __uint_as_float((b1[h] << L1_SHIFT) | (b2 << L2_SHIFT) | L2_LOW);
+                    tau2f[h] = __double2float_rd(screen_margin(tau0[h], p, R));
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int h = 0; h < QPW; h++) {
+            if (!active[h] || lane != 0) continue;
+            const int ql = w * QPW + h;
+            const int c = s_count[ql], c0 = s_count0[ql];
+            const bool kvalid = k[h] >= 1 && k[h] <= Npmax;
+            if (!retry_pass) {
+                const bool done = ok[h] && c0 >= k[h] && c <= Cmax;
+                retry[q[h]] = (ok[h] && !done) ? 1 : 0;
+                cand_count[q[h]] = done ? c : 0;
+                if (status) status[q[h]] = kvalid ? LAGP_OK : LAGP_EINVAL;
+            } else if (ok[h]) {
+                // exact retry: fewer rows than N' under the threshold only happens
+                // with non-finite distances (NaN or overflowing coordinates)
+                cand_count[q[h]] = (c0 >= k[h] && c <= Cmax) ? c : 0;
+                if (status) status[q[h]] = c0 < k[h] ? LAGP_EINVAL : (c > Cmax ? LAGP_ENOMEM : LAGP_OK);
             }
         }
         __syncthreads();
-        if (ok && pass == 0) {
-            find_bin(hist + w * HB, (uint32_t)k, lane, b1, before);
-            __syncwarp();
-            for (int b = lane; b < HB; b += 32) hist[w * HB + b] = 0;
-        } else if (ok && pass == 1) {
-            uint32_t b2, before2;
-            find_bin(hist + w * HB, (uint32_t)k - before, lane, b2, before2);
-            float tau = __uint_as_float((b1 << 20) | (b2 << 9) | 0x1FFu);
-            tau2 = screen_margin(tau, p, R);
-        }
-        __syncthreads();
-    }
-    if (active && lane == 0) {
-        cand_count[q] = ok ? s_count[w] : 0;
-        // fewer rows than N' under the threshold only happens with non-finite
-        // distances (NaN or overflowing coordinates)
-        if (status)
-            status[q] = !ok || s_count[w] < k ? LAGP_EINVAL
-                                              : (s_count[w] > Cmax ? LAGP_ENOMEM : LAGP_OK);
     }
 }
 
@@ -277,10 +403,13 @@ template <int P>
 void launch_screen(dim3 grid, size_t smem, cudaStream_t st, const float *X32, int64_t N, int p,
                    const void *Xref, lagp_dtype dt, int64_t M, const int32_t *Np, int32_t Npmax,
                    const unsigned long long *Rb, int32_t *cand, int32_t Cmax, int32_t *cc,
-                   int32_t *status) {
+                   int32_t *status, int64_t stride, int32_t *retry, int *counters) {
     cudaFuncSetAttribute(knn_screen<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // sampled threshold, then the exact retry of the flagged queries
     knn_screen<P><<<grid, SCREEN_THREADS, smem, st>>>(X32, N, p, Xref, dt, M, Np, Npmax, Rb, cand,
-                                                      Cmax, cc, status);
+                                                      Cmax, cc, status, stride, retry, 0, counters);
+    knn_screen<P><<<grid, SCREEN_THREADS, smem, st>>>(X32, N, p, Xref, dt, M, Np, Npmax, Rb, cand,
+                                                      Cmax, cc, status, 1, retry, 1, counters + 1);
 }
 
 }  // namespace
@@ -290,13 +419,16 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
                        int32_t *idx, int32_t *status) {
     cudaStream_t st = ctx->stream;
     const int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
-    // meta: R bits (8 bytes), then per-query candidate counts
-    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, 256 + (size_t)M * 4));
+    // meta: R bits (8 bytes) and two block counters, then per-query candidate
+    // counts and retry flags
+    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, 256 + (size_t)M * 8));
     int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
     if (!meta || !cand) return LAGP_ENOMEM;
     unsigned long long *Rbits = reinterpret_cast<unsigned long long *>(meta);
     int32_t *cc = reinterpret_cast<int32_t *>(meta + 256);
-    LAGP_CUDA(ctx, cudaMemsetAsync(Rbits, 0, 8, st));
+    int32_t *retry = cc + M;
+    int *counters = reinterpret_cast<int *>(meta + 64);
+    LAGP_CUDA(ctx, cudaMemsetAsync(meta, 0, 256, st));
     const float *X32;
     if (dtype == LAGP_F64) {
         float *x32 = static_cast<float *>(lagp_ws(ctx, WS_KNN_X32, (size_t)N * p * 4));
@@ -311,15 +443,19 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     }
     LAGP_CUDA(ctx, cudaGetLastError());
 
-    size_t smem = (size_t)QB * HB * 4 + (size_t)TILE_FLOATS * 4 + (size_t)QB * p * 4;
-    dim3 grid((unsigned)((M + QB - 1) / QB));
+    size_t smem = (size_t)QB * HB * 4 + 2 * (size_t)p * (tile_len(p) + 1) * 4 + (size_t)QB * p * 4;
+    // persistent grid: two CTAs per SM, blocks of QB queries from a counter
+    const int64_t nblk = (M + QB - 1) / QB;
+    dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)ctx->num_sms * 2));
+    // sample stride: about 8 N' sampled rows per candidate set, 1 (exact) for small designs
+    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(64, N / (8 * (int64_t)Npmax)));
     switch (p) {
-        case 2: launch_screen<2>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status); break;
-        case 3: launch_screen<3>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status); break;
-        case 8: launch_screen<8>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status); break;
-        default: launch_screen<0>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status); break;
+        case 2: launch_screen<2>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
+        case 3: launch_screen<3>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
+        case 8: launch_screen<8>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
+        default: launch_screen<0>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
     }
-    ctx->launches++;
+    ctx->launches += 2;
     LAGP_CUDA(ctx, cudaGetLastError());
 
     int Cp = 1;
