@@ -109,6 +109,20 @@ lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in);
  * points), for launch accounting. */
 int64_t lagp_launch_count(const lagp_ctx *ctx);
 
+/* Autotuner.  Times the ALC search (a2..a6, or a2..a7 when Y is not NULL) on
+ * a sample of the given problem (its first min(M, 16 x SMs) locations) for
+ * every admissible number of resident CTAs per SM of the persistent kernel,
+ * and records the fastest for problems of this shape (precision, N'
+ * capacity, n_max, p, with or without prediction) on this context; later
+ * calls with tuning.ctas_per_sm == 0 use it.  Synchronises the stream.
+ * Arguments as lagp_alc_predict; *best_ctas_per_sm (may be NULL) receives the
+ * choice. */
+lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                          const void *Xref, int64_t M, const int32_t *idx, const int32_t *Nprime,
+                          int32_t Nprime_max, int32_t n0, const int32_t *n, int32_t n_max,
+                          const double *d, double g, lagp_precision prec, const void *Y,
+                          int32_t *best_ctas_per_sm);
+
 /* ---------------------------------------------------------------- a1: kNN
  * Exact N'-nearest-neighbour candidate sets (Sec. 3.1: the ALC search is
  * restricted to the N' nearest neighbours of x; Fig. 1 step 2(a) takes the

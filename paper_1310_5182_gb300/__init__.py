@@ -8,7 +8,7 @@ library has not been built: there is no CPU fallback.  The build module
 (paper_1310_5182_gb300.build) imports without the library.
 """
 _BINDING = ("LagpError", "context", "get_tuning", "lagp_agp", "lagp_alc_predict", "lagp_alc_select",
-            "lagp_knn",
+            "lagp_knn", "lagp_autotune",
             "lagp_mle_step", "lagp_predict", "lagp_predict_grad", "lagp_predict_noalloc",
             "launch_count", "library",
             "set_tuning")
@@ -20,4 +20,7 @@ def __getattr__(name):
     if name in _BINDING:
         from . import lagp
         return getattr(lagp, name)
+    if name in ("local_gp", "local_loglik", "LocalGP", "LocalLogLik"):
+        from . import autograd
+        return getattr(autograd, name)
     raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

@@ -326,7 +326,7 @@ lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a) {
     cudaFuncSetAttribute(alc_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f64_kernel, F64_THREADS, smem);
-    int per_sm = ctx->tuning.ctas_per_sm > 0 ? ctx->tuning.ctas_per_sm : 2;
+    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key("alc_f64", 0, a.nmax, a.p, a.mean != nullptr), 2);
     if (occ > 0 && per_sm > occ) per_sm = occ;
     int64_t grid = (int64_t)ctx->num_sms * per_sm;
     if (grid > a.M) grid = a.M;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 
 #include "lagp.h"
@@ -18,6 +19,7 @@ enum WsSlot {
     WS_ALC_COUNTER,   // persistent-grid work counters
     WS_GP_MAT,        // predict / MLE per-CTA matrices
     WS_AGP_IO,        // lagp_agp device copies of inputs and outputs
+    WS_TUNE,          // autotuner trial outputs
     WS_NSLOTS
 };
 
@@ -31,7 +33,16 @@ struct lagp_ctx {
     std::string err;
     lagp_tuning tuning = {0, 0, 8, 0.5};
     int64_t launches = 0;
+    // autotuned resident CTAs per SM, keyed by the ALC problem shape
+    std::map<std::string, int> tuned_ctas;
+    int tune_override = 0;  // set by the autotuner while it times a candidate
 };
+
+// Shape key of an ALC launch for the autotuner's table.
+std::string alc_shape_key(const char *kernel, int cpt, int nmax, int p, bool fused);
+// Resident CTAs per SM for an ALC launch: the autotuner's trial value, the
+// user's tuning, the tuned table, or the kernel's default.
+int alc_ctas_per_sm(lagp_ctx *ctx, const std::string &key, int default_cps);
 
 // status helpers (lagp_api.cu)
 lagp_status lagp_fail(lagp_ctx *ctx, lagp_status s, const std::string &msg);

@@ -67,12 +67,14 @@ def _load():
                                   P, P, P, P, P]
     lib.lagp_predict_grad.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P,
                                       P, P, P, P, P]
+    lib.lagp_autotune.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, I32, P, I32, P, D,
+                                  ctypes.c_int, P, P]
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
-              "lagp_predict_grad",
+              "lagp_predict_grad", "lagp_autotune",
               "lagp_agp"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
@@ -174,6 +176,26 @@ def set_tuning(device=None, **fields):
     for k, v in fields.items():
         setattr(t, k, v)
     _check(_lib.lagp_set_tuning(ctx, ctypes.byref(t)), ctx, "lagp_set_tuning")
+
+
+def lagp_autotune(X, Xref, idx, n0, n, d, g, prec="f32bulk", Y=None, Nprime=None, n_max=None):
+    """Time the ALC search for each admissible resident-CTA count on a sample
+    of this problem and record the fastest on the context.  Returns it."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M, Npmax = idx.shape
+    nt, npp = _opt_i32(n, M, X.device, "n")
+    if n_max is None:
+        n_max = int(nt.max().item()) if nt is not None and M else int(n)
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    dt = _per_loc_f64(d, M, X.device)
+    best = ctypes.c_int32(0)
+    _check(_lib.lagp_autotune(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref", X.dtype), M,
+                              _dev(idx, "idx", torch.int32), Npp, Npmax, int(n0), npp, int(n_max),
+                              _dev(dt, "d"), float(g), _PREC[prec],
+                              None if Y is None else _dev(Y, "Y", X.dtype), ctypes.byref(best)),
+           ctx, "lagp_autotune")
+    return int(best.value)
 
 
 def launch_count(device=None) -> int:

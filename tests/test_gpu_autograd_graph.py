@@ -1,0 +1,111 @@
+"""GPU: the adjoint behind torch.autograd (against five-point finite
+differences of the forward kernels), and the search captured in a CUDA graph
+(replays identical to eager calls)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1310_5182_gb300 as lib
+    return lib
+
+
+def _setup(L, seed=51):
+    w = W.toy2d(seed=seed, N=4000, M=24, Np=200, n=25)
+    dev = torch.device("cuda", 0)
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    idx, _ = L.lagp_knn(X, Xr, 200)
+    sel = L.lagp_alc_select(X, Xr, idx, 6, 25, w.d, w.g, prec="f64")["sel"]
+    return w, X, Y, Xr, sel
+
+
+def _fd5(f, x, h):
+    return (8 * (f(x + h) - f(x - h)) - (f(x + 2 * h) - f(x - 2 * h))) / (12 * h)
+
+
+def test_local_gp_gradients_match_finite_differences(L):
+    w, X, Y, Xr, sel = _setup(L)
+    d = torch.full((24,), 0.4, dtype=torch.float64, device=X.device, requires_grad=True)
+    g = torch.tensor(2e-4, dtype=torch.float64, device=X.device, requires_grad=True)
+    wm = torch.linspace(0.5, 1.5, 24, dtype=torch.float64, device=X.device)
+    mean, s2 = L.local_gp(d, g, X, Y, Xr, sel, 25)
+    (wm * mean + 3.0 * s2).sum().backward()
+
+    def objective(dd, gg):
+        m, s = L.local_gp(dd, gg, X, Y, Xr, sel, 25)
+        return (wm * m + 3.0 * s).sum().item()
+
+    with torch.no_grad():
+        for i in (0, 7, 23):
+            def fi(t):
+                dd = d.detach().clone()
+                dd[i] = t
+                return objective(dd, g.item())
+            fd = _fd5(fi, 0.4, 1e-3 * 0.4)
+            assert abs(d.grad[i].item() - fd) <= 1e-6 * max(1.0, abs(fd))
+        fdg = _fd5(lambda t: objective(d.detach(), t), 2e-4, 1e-2 * 2e-4)
+        assert abs(g.grad.item() - fdg) <= 1e-5 * max(1.0, abs(fdg))
+
+
+def test_local_loglik_gradients(L):
+    from oracle import oracle as O
+    w, X, Y, Xr, sel = _setup(L, seed=52)
+    d = torch.linspace(0.2, 1.2, 24, dtype=torch.float64, device=X.device).requires_grad_(True)
+    ll = L.local_loglik(d, w.g, X, Y, Xr, sel, 25)
+    ll.sum().backward()
+    ref = O.llik(w.X, w.Y, sel.cpu().numpy(), 25, d.detach().cpu().numpy(), w.g)
+    np.testing.assert_allclose(ll.detach().cpu().numpy(), ref["llik"], rtol=1e-9)
+    np.testing.assert_allclose(d.grad.cpu().numpy(), ref["dllik"], rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["f32bulk", "f64"])
+def test_search_captured_in_cuda_graph(L, prec):
+    """kNN and the fused search+prediction, captured once and replayed: the
+    persistent kernels and their work counters (reset by captured memsets)
+    give the same designs and predictions as eager calls."""
+    w = W.borehole(seed=53, N=20_000, M=300, Np=400, n=30)
+    dev = torch.device("cuda", 0)
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    # per-location arguments as device tensors made before capture (a Python
+    # scalar would need a host-to-device copy inside the capture)
+    n_t = torch.full((w.M,), 30, dtype=torch.int32, device=dev)
+    d_t = torch.full((w.M,), w.d, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        idx, _ = L.lagp_knn(X, Xr, 400)  # warm: workspaces are sized outside capture
+        eager = L.lagp_alc_predict(X, Y, Xr, idx, 6, n_t, d_t, w.g, prec=prec, n_max=30)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        idx_g, _ = L.lagp_knn(X, Xr, 400)
+        out_g = L.lagp_alc_predict(X, Y, Xr, idx_g, 6, n_t, d_t, w.g, prec=prec, n_max=30)
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(idx_g, idx)
+        assert torch.equal(out_g["sel"], eager["sel"])
+        assert torch.equal(out_g["mean"], eager["mean"])
+        assert torch.equal(out_g["s2"], eager["s2"])
+
+
+def test_autotune_picks_a_grid_and_results_do_not_depend_on_it(L):
+    """The autotuner times every admissible resident-CTA count; the designs
+    (one persistent CTA per location at a time) must not depend on it."""
+    w = W.borehole(seed=54, N=20_000, M=700, Np=300, n=25)
+    dev = torch.device("cuda", 0)
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    idx, _ = L.lagp_knn(X, Xr, 300)
+    before = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g)
+    best = L.lagp_autotune(X, Xr, idx, 6, 25, w.d, w.g, prec="f32bulk", Y=Y)
+    assert 1 <= best <= 4
+    after = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g)
+    assert torch.equal(before["sel"], after["sel"])
+    assert torch.equal(before["mean"], after["mean"])
