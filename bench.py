@@ -68,13 +68,48 @@ def workload_for_rank(rank: int, M=None):
 
 def work_per_location(n0, n, Np):
     """Algorithmic counts per location: ALC candidate evaluations of the
-    greedy search, E = sum_{j=n0}^{n-1} (N' - j), and the bytes of the
-    whitened candidate panel U that the FP32-bulk screen reads and writes,
-    sum_{j=0}^{n-2} (N' j + N') * 4 (one FP32 column read per design row and
-    one column written per step)."""
+    greedy search, E = sum_{j=n0}^{n-1} (N' - j), and the FP32 flops of the
+    bulk screen's Schur recurrence: after step j every unchosen candidate
+    takes a dot product of length j with the pivot column (2j), its squared
+    distance to the new design point (3p), and the updates of u, v, r and the
+    score (8)."""
     E = sum(Np - j for j in range(n0, n))
-    U_bytes = sum((Np * j + Np) * 4 for j in range(0, n - 1))
-    return E, U_bytes
+    return E
+
+
+def fp32_flops_per_location(n, Np, p):
+    return sum((Np - j - 1) * (2 * j + 3 * p + 8) for j in range(0, n - 1))
+
+
+def fp64_flops(work, M, n, p, fused):
+    """FP64 flops of the FP32-bulk search from the kernel's work counters
+    (sums over steps of the contenders re-scored, n_c, of n_c j and n_c j^2).
+    Per contender at design size j: its j + 1 kernel values (p subtracts and
+    p fused multiply-adds for the squared distance, the scale by -1/d, and the
+    20 flops of the table-driven exp), the contraction with [K^{-1} | a (|
+    alpha)] (2 j (j + e), e = 2 with the fused prediction, else 1), k^T b (2j)
+    and 12 flops of scalars (Eqs. piedef, dxy).  Per step: mu b (j), the
+    symmetric rank-one update of K^{-1} (j (j + 1)), the updates of a (and
+    alpha) (2 j e) and 10 flops of scalars."""
+    e = 2 if fused else 1
+    cf = 3 * p + 21
+    per_con = work["rescored"] * (cf + 12) + work["rescored_j"] * (cf + 2 * e + 2) + 2 * work["rescored_j2"]
+    per_step = M * sum(j * j + (2 + 2 * e) * j + 10 for j in range(n))
+    return per_con + per_step
+
+
+# DRAM traffic (read + write) of the ALC kernel per location, from one ncu
+# capture of the kernel whose sources hash to `sha256` (the capture and its
+# command are summarised under profiles/); null for any other source.
+ALC_TRAFFIC = {"sha256": None, "dram_bytes_per_location": None}
+
+
+def alc_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("alc_f32.cu", "exp64.cuh", "device_util.cuh", "lagp_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1310_5182_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 # ------------------------------------------------------------------ clocks
@@ -222,6 +257,7 @@ def run_ours(args, rank, world, local_rank):
         time.sleep(0.5)  # let nvidia-smi start sampling
         clk.mark()
     launches0 = L.launch_count(dev)
+    L.alc_work(dev)  # reset the work counters: the timed steps' counts follow
     step_ms, alc_ms = [], []
     for _ in range(args.steps):
         flush.zero_()  # evict the design and panels from L2 between timed steps
@@ -235,6 +271,7 @@ def run_ours(args, rank, world, local_rank):
         step_ms.append(e0.elapsed_time(e1))
         alc_ms.append(a0.elapsed_time(a1))
     launches = (L.launch_count(dev) - launches0)
+    work = L.alc_work(dev)
     clocks = clk.stop() if clk else None
     t_local = sum(step_ms) / 1e3
     t = torch.tensor([t_local], dtype=torch.float64, device=dev)
@@ -324,19 +361,31 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    E, U_bytes = work_per_location(n0, n, Np)
+    E = work_per_location(n0, n, Np)
     alc_avg = statistics.mean(alc_ms) / 1e3
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = M * U_bytes / alc_avg / 1e9
-    roofline = {"bound": "hbm", "kernel": "alc_f32_kernel", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": M * U_bytes}
+    # peaks: the dominant kernel is bound by the FP64 unit (the re-score and
+    # the update of K^{-1}); FP64 and FP32 peaks from the unit counts and the
+    # SM clock sampled during the timed region
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak = sms * 4 * mhz * 1e6 / 1e12      # 2 FP64 FMA lanes / cycle / SM
+    fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # 128 FP32 FMA lanes / cycle / SM
+    per_launch = {k: v / args.steps for k, v in work.items()}
+    fl64 = fp64_flops(per_launch, M, n, w.p, True)
+    fl32 = M * fp32_flops_per_location(n, Np, w.p)
+    achieved = fl64 / alc_avg / 1e12
+    traffic = None
+    if ALC_TRAFFIC["sha256"] == alc_source_hash() and ALC_TRAFFIC["dram_bytes_per_location"]:
+        traffic = ALC_TRAFFIC["dram_bytes_per_location"] * M
+    roofline = {"bound": "alu", "kernel": "alc_f32_kernel", "unit": "TFLOP/s", "achieved": achieved,
+                "peak": fp64_peak, "frac": achieved / fp64_peak, "traffic": traffic,
+                "peak_source": f"derived: FP64, {sms} SMs x 4 flop/cycle x {mhz:.0f} MHz (sampled)",
+                "fp64_flops_per_launch": fl64,
+                "rescored_per_step": work["rescored"] / max(1, work["locations"]) / n,
+                "fp32_screen": {"achieved": fl32 / alc_avg / 1e12, "peak": fp32_peak,
+                                "frac": fl32 / alc_avg / 1e12 / fp32_peak, "unit": "TFLOP/s",
+                                "flops_per_launch": fl32}}
     cpu = None
     if not args.no_cpu and world == 1:
         S = 1024

@@ -109,6 +109,24 @@ lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in);
  * points), for launch accounting. */
 int64_t lagp_launch_count(const lagp_ctx *ctx);
 
+/* Work counters of the FP32-bulk ALC search (not part of the paper's method;
+ * they measure the FP64 re-score that the FP32 screen leaves, Eq. dxy):
+ *   out[0]  locations searched
+ *   out[1]  sum over steps of the contenders re-scored in FP64 (n_c)
+ *   out[2]  sum over steps of n_c * j   (j = design size at the step)
+ *   out[3]  sum over steps of n_c * j^2
+ * summed over every F32BULK search launched on this context since it was
+ * created or last read.  Reading synchronises the context's stream and
+ * resets the counters to zero. */
+lagp_status lagp_alc_work(lagp_ctx *ctx, uint64_t out[4]);
+
+/* Diagnostic: the library's own FP64 exponential (Tang's table-driven
+ * method, used for the kernel values of the FP32-bulk re-score) and the CUDA
+ * library's exp, both evaluated at the n device values a[] into the device
+ * arrays out_tang[] and out_lib[] (enqueued on the context's stream). */
+lagp_status lagp_exp64_check(lagp_ctx *ctx, const double *a, int64_t n, double *out_tang,
+                             double *out_lib);
+
 /* Autotuner.  Times the ALC search (a2..a6, or a2..a7 when Y is not NULL) on
  * a sample of the given problem (its first min(M, 16 x SMs) locations) for
  * every admissible number of resident CTAs per SM of the persistent kernel,

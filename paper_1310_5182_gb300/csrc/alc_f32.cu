@@ -40,6 +40,7 @@
 #include <algorithm>
 
 #include "device_util.cuh"
+#include "exp64.cuh"
 #include "lagp_internal.h"
 
 namespace {
@@ -94,20 +95,25 @@ __device__ __forceinline__ void store_vec(float *p, const float (&v)[CPT]) {
 struct F32Params {
     AlcArgs a;
     int *counter;
+    unsigned long long *work;  // 4 counters: locations, sum ncon, sum ncon*j, sum ncon*j^2
     float *U_ws;      // per CTA: nmax x Npad (whitened panel U[i][c])
     float *C_ws;      // per CTA: p x Npad (FP32 candidate coordinates C[i][c])
-    double *K_ws;     // per CTA: Npad (FP64 K(x_c, x), computed once per location)
     int Npad;         // F32_THREADS * CPT
     int tmax;         // rescore_max
     float rel;        // rescore_rel (cap of the contender margin)
 };
 
-// Rows [k0, k1) of the contraction b = K^{-1} kc: lane t writes
-// sum_{kk in [k0,k1)} K^{-1}[kk][t] kc[kk] for its columns t = lane + 32 r
-// (rows of the symmetric K^{-1} have leading dimension ld, a multiple of 32).
+// Contenders kept in the first (static) part of the appended list; at least
+// the largest rescore_max.
+constexpr int LCAP = 32;
+
+// Rows [k0, k1) of the contraction with the symmetric K^{-1} and the two
+// vectors stored beside it: lane t writes sum_{kk in [k0,k1)} S[kk][t] kc[kk]
+// for its columns t = lane + 32 r < jo, where S[kk][t] is K^{-1} for t < j,
+// a = K^{-1} k_j(x) for t = j and alpha = K^{-1} Y_j for t = j + 1.
 template <int JQ>
 __device__ __forceinline__ void partial_contract(const double *kc, const double *Kinv, int ld, int k0,
-                                                 int k1, int j, int lane, double *out) {
+                                                 int k1, int jo, int lane, double *out) {
     double b0[JQ], b1[JQ];
 #pragma unroll
     for (int r = 0; r < JQ; r++) b0[r] = b1[r] = 0.0;
@@ -129,7 +135,7 @@ __device__ __forceinline__ void partial_contract(const double *kc, const double 
     }
 #pragma unroll
     for (int r = 0; r < JQ; r++)
-        if (lane + 32 * r < j) out[lane + 32 * r] = b0[r] + b1[r];
+        if (lane + 32 * r < jo) out[lane + 32 * r] = b0[r] + b1[r];
 }
 
 // Integer key with the order of the doubles (for comparisons off the FP64 pipe)
@@ -161,42 +167,44 @@ alc_f32_kernel(F32Params P) {
     const AlcArgs &a = P.a;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, Npmax = a.Npmax, Npad = P.Npad, tmax = P.tmax;
-    const int ld = (nmax + 31) & ~31;
-    double *Kinv = reinterpret_cast<double *>(smem_raw);       // (nmax+1) x ld
-    double *kx = Kinv + (size_t)(nmax + 1) * ld;               // ld: k_j(x)
-    double *yd = kx + ld;                                      // ld: responses of the design
-    double *alpha = yd + ld;                                   // ld: K_j^{-1} Y_j
-    double *xd = alpha + ld;                                   // nmax x p: design coordinates
-    double *xq = xd + (size_t)nmax * p;                        // p: reference location
-    double *con_b = xq + p;                                    // tmax x ld: K^{-1} k_j(x_c)
-    double *con_k = con_b + (size_t)tmax * ld;                 // tmax x ld: k_j(x_c), FP64
-    double *con_x = con_k + (size_t)tmax * ld;                 // tmax x p: coordinates, FP64
-    float *con_u = reinterpret_cast<float *>(con_x + (size_t)tmax * p);  // tmax x ld: U column
-    float *con_c = con_u + (size_t)tmax * ld;                  // tmax x p: coordinates, FP32
-    // max(8, tmax) x ld partial contractions (one row per R2 job)
-    double *cpart = reinterpret_cast<double *>(con_c + (((size_t)tmax * p + 1) & ~(size_t)1));
-    float *list_s = reinterpret_cast<float *>(cpart + (size_t)max(F32_WARPS, tmax) * ld);  // Npad scores
-    int *list_c = reinterpret_cast<int *>(list_s + Npad);      // Npad: their slots
-    int *list_r = list_c + Npad;                               // Npad: their design rows
-
-    __shared__ int s_loc, s_bad, s_ncon, s_win;
-    __shared__ int w_cnt[F32_WARPS];
-    __shared__ float w_max[F32_WARPS];
-    __shared__ int con_slot[32], con_row[32];
-    __shared__ float con_s32[32], con_err[32];
-    __shared__ double con_delta[32], con_minv[32], con_mu[32], con_kxb[32], con_kap[32], con_ry[32],
-        con_y[32], con_dot[3][32];
-    __shared__ long long con_key[32];
-    __shared__ double s_psi, s_qx;
-    __shared__ float s_vstar, s_covstar, s_err;
     const bool fused = a.mean != nullptr;
+    const int extra = fused ? 2 : 1;        // columns of a (and alpha) beside K^{-1}
+    const int ld = (nmax + 3) & ~1;         // >= nmax + 2, even
+    double *Kinv = reinterpret_cast<double *>(smem_raw);        // (nmax+1) x ld
+    double *kx = Kinv + (size_t)(nmax + 1) * ld;                // nmax (even): k_j(x)
+    double *xd = kx + ((nmax + 1) & ~1);                        // nmax x p: design coordinates
+    double *xq = xd + (size_t)nmax * p;                         // p (even): reference location
+    double *etab = xq + ((p + 1) & ~1);                         // 64: table of exp64_tang
+    double *con_k = etab + 64;                                  // tmax x ld: k_j(x_c), FP64
+    double *con_b = con_k + (size_t)tmax * ld;                  // tmax x ld: K^{-1} k_j(x_c)
+    double *cpart = con_b + (size_t)tmax * ld;                  // max(8,tmax) x ld partials;
+                                                                // row 0 then holds mu b of the winner
+    // the appended list beyond its first LCAP entries shares the space of
+    // con_k.. (it is dead before the re-score starts)
+    float *ov_s = reinterpret_cast<float *>(con_k);
+    int *ov_slot = reinterpret_cast<int *>(ov_s + Npad);
+    const size_t union_doubles =
+        max((size_t)Npad, ((size_t)2 * tmax + max(F32_WARPS, tmax)) * ld);
+    float *w_u = reinterpret_cast<float *>(con_k + union_doubles);  // ld: U column of the winner
+    float *w_c = w_u + ld;                                            // p: its FP32 coordinates
+    double *mb = cpart;
+
+    __shared__ int s_loc, s_bad, s_total, s_wl;
+    __shared__ float w_max[F32_WARPS];
+    __shared__ int lst_slot[LCAP], lst_row[LCAP], top_slot[LCAP], top_row[LCAP];
+    __shared__ float lst_s[LCAP], top_s[LCAP];
+    __shared__ double con_kap[LCAP], con_y[LCAP], con_quad[LCAP], con_kxb[LCAP], con_yb[LCAP];
+    __shared__ double s_mu, s_ex, s_ry, s_kap, s_kxb, s_dl, s_psi, s_qx;
+    __shared__ float s_vstar, s_covstar, s_err;
+    __shared__ unsigned long long s_work[4];
 
     float *U = P.U_ws + (size_t)blockIdx.x * nmax * Npad;
     float *Cg = P.C_ws + (size_t)blockIdx.x * p * Npad;
-    double *kap64 = P.K_ws + (size_t)blockIdx.x * Npad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = tid * CPT;  // first candidate slot of this thread
     const int rot = blockIdx.x & (F32_WARPS - 1);
+    if (tid < 64) etab[tid] = exp64_table_g[tid];
+    if (tid < 4) s_work[tid] = 0ull;
 
     for (;;) {
         if (tid == 0) s_loc = atomicAdd(P.counter, 1);
@@ -233,32 +241,21 @@ alc_f32_kernel(F32Params P) {
             continue;
         }
 
-        // ---- per-location set-up: coordinates, kappa, initial FP32 state
+        // ---- per-location set-up: coordinates and the initial FP32 state
         for (int i = tid; i < p; i += F32_THREADS) xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
         for (int e = tid; e < p * Npad; e += F32_THREADS) {
             int i = e / Npad, c = e - i * Npad;
             Cg[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
         }
-        const double inv_d64 = 1.0 / d;
-        __syncthreads();
-        // K(x_c, x) in FP64 for every candidate, once per location (the FP64
-        // re-score then reads it instead of recomputing an exponential)
-        for (int c = tid; c < k; c += F32_THREADS) {
-            const int32_t r = cands[c];
-            double s0 = 0.0, s1 = 0.0;
-            int i = 0;
-            for (; i + 2 <= p; i += 2) {
-                const double d0 = load_coord64(a.X, r, p, i, a.dtype) - xq[i];
-                const double d1 = load_coord64(a.X, r, p, i + 1, a.dtype) - xq[i + 1];
-                s0 = fma(d0, d0, s0);
-                s1 = fma(d1, d1, s1);
-            }
-            if (i < p) {
-                const double d0 = load_coord64(a.X, r, p, i, a.dtype) - xq[i];
-                s0 = fma(d0, d0, s0);
-            }
-            kap64[c] = exp(-(s0 + s1) * inv_d64);
+        const double inv_d64 = 1.0 / d, onepg = 1.0 + g;
+        if (tid == 0) {
+            s_err = ERR_INIT;
+            s_psi = 0.0;
+            s_qx = 0.0;
+            s_total = 0;
+            s_work[0] += 1ull;
         }
+        __syncthreads();
         const float inv_d = (float)(1.0 / d);
         const float gf = fmaxf((float)g, FLT_MIN);
         float v[CPT], cov[CPT], score[CPT];
@@ -282,13 +279,12 @@ alc_f32_kernel(F32Params P) {
             for (int r = 0; r < CPT; r++) {
                 const int c = c0 + r;
                 rows[r] = c < k ? cands[c] : INT32_MAX;
-                v[r] = (float)(1.0 + g);
+                v[r] = (float)onepg;
                 cov[r] = __expf(-s[r] * inv_d);  // K(x_c, x), no nugget
                 score[r] = c < k ? cov[r] * cov[r] / v[r] : -1.f;
                 if (c >= k) chosen |= 1u << r;  // padding slots never compete
             }
         }
-
         {
             float wm = -FLT_MAX;
 #pragma unroll
@@ -299,23 +295,20 @@ alc_f32_kernel(F32Params P) {
             if (lane == 0) w_max[warp] = wm;
         }
         int status = LAGP_OK;
-        if (tid == 0) {
-            s_err = ERR_INIT;
-            s_psi = 0.0;
-            s_qx = 0.0;
-        }
-        __syncthreads();
         for (int j = 0; j < nm; j++) {
-            // ---------------- contenders for design index j
+            const int jo = j + extra;  // outputs of the contraction: K^{-1} k, a^T k (, alpha^T k)
+            // ---------------- contenders for design index j.  The barrier
+            // orders the last FP32 pass (per-warp maxima, column j-1 of U) and
+            // the last update before everything below.
+            __syncthreads();
             if (j < a.n0) {
                 if (tid == 0) {
-                    s_ncon = 1;
-                    con_slot[0] = j;  // Fig. 1 step 2(a): nearest neighbours in order
-                    con_row[0] = cands[j];
-                    con_s32[0] = 0.f;
+                    lst_slot[0] = j;  // Fig. 1 step 2(a): nearest neighbours in order
+                    lst_row[0] = cands[j];
+                    lst_s[0] = 0.f;
+                    s_total = 1;
                 }
             } else {
-                __syncthreads();  // the per-warp maxima of the last FP32 pass
                 const float margin = fminf(P.rel, fmaxf(MARGIN_MIN, MARGIN_KAPPA * s_err));
                 float gmax = w_max[0];
 #pragma unroll
@@ -332,61 +325,64 @@ alc_f32_kernel(F32Params P) {
                     const int t = __shfl_up_sync(LAGP_FULL_MASK, incl, o);
                     if (lane >= o) incl += t;
                 }
-                if (lane == 31) w_cnt[warp] = incl;
-                __syncthreads();
-                int off = 0, total = 0;
-#pragma unroll
-                for (int w = 0; w < F32_WARPS; w++) {
-                    off += w < warp ? w_cnt[w] : 0;
-                    total += w_cnt[w];
-                }
-                int pos = off + incl - mine;  // slot order: deterministic
+                const int wtot = __shfl_sync(LAGP_FULL_MASK, incl, 31);
+                int base = 0;
+                if (lane == 31 && wtot > 0) base = atomicAdd(&s_total, wtot);
+                base = __shfl_sync(LAGP_FULL_MASK, base, 31);
+                // list order depends on the warps' arrival; the contender set,
+                // and every result, does not
+                int pos = base + incl - mine;
 #pragma unroll
                 for (int r = 0; r < CPT; r++)
                     if (flags >> r & 1u) {
-                        list_s[pos] = score[r];
-                        list_c[pos] = c0 + r;
-                        list_r[pos] = rows[r];
+                        if (pos < LCAP) {
+                            lst_s[pos] = score[r];
+                            lst_slot[pos] = c0 + r;
+                            lst_row[pos] = rows[r];
+                        } else {
+                            ov_s[pos] = score[r];
+                            ov_slot[pos] = c0 + r;
+                        }
                         pos++;
                     }
-                __syncthreads();
-                if (warp == 0) {
-                    if (total <= tmax) {  // every flagged candidate is re-scored
-                        for (int e = lane; e < total; e += 32) {
-                            con_slot[e] = list_c[e];
-                            con_row[e] = list_r[e];
-                            con_s32[e] = list_s[e];
-                        }
-                        if (lane == 0) s_ncon = total;
-                    } else {  // the best tmax by FP32 score, ties to the lower row
-                        int ncon = 0;
-                        for (int t = 0; t < tmax; t++) {
-                            float bs = -FLT_MAX;
-                            int brow = INT32_MAX, bpos = -1;
-                            for (int e = lane; e < total; e += 32)
-                                if (list_c[e] >= 0 &&
-                                    (list_s[e] > bs || (list_s[e] == bs && list_r[e] < brow))) {
-                                    bs = list_s[e];
-                                    brow = list_r[e];
-                                    bpos = e;
-                                }
-                            warp_best3(bs, brow, bpos);
-                            if (bpos < 0) break;
-                            if (lane == 0) {
-                                con_slot[ncon] = list_c[bpos];
-                                con_row[ncon] = brow;
-                                con_s32[ncon] = bs;
-                                list_c[bpos] = -1;
-                            }
-                            __syncwarp();
-                            ncon++;
-                        }
-                        if (lane == 0) s_ncon = ncon;
-                    }
-                }
             }
             __syncthreads();
-            const int ncon = s_ncon;
+            const int total = s_total;
+            if (total > tmax) {  // keep the best tmax by FP32 score, ties to the lower row
+                if (warp == 0) {
+                    for (int t = 0; t < tmax; t++) {
+                        float bs = -FLT_MAX;
+                        int brow = INT32_MAX, bpos = -1;
+                        for (int e = lane; e < total; e += 32) {
+                            const int sl = e < LCAP ? lst_slot[e] : ov_slot[e];
+                            if (sl < 0) continue;
+                            const float sc = e < LCAP ? lst_s[e] : ov_s[e];
+                            const int rw = e < LCAP ? lst_row[e] : cands[sl];
+                            if (sc > bs || (sc == bs && rw < brow)) {
+                                bs = sc;
+                                brow = rw;
+                                bpos = e;
+                            }
+                        }
+                        warp_best3(bs, brow, bpos);
+                        if (bpos < 0) break;
+                        if (lane == 0) {
+                            const bool lo = bpos < LCAP;
+                            top_slot[t] = lo ? lst_slot[bpos] : ov_slot[bpos];
+                            top_row[t] = brow;
+                            top_s[t] = bs;
+                            if (lo) lst_slot[bpos] = -1;
+                            else ov_slot[bpos] = -1;
+                        }
+                        __syncwarp();
+                    }
+                }
+                __syncthreads();
+            }
+            const int ncon = min(total, tmax);
+            const int *cslot = total > tmax ? top_slot : lst_slot;
+            const int *crow = total > tmax ? top_row : lst_row;
+            const float *cs32 = total > tmax ? top_s : lst_s;
             if (ncon < 1) {
                 status = LAGP_ENOTPD;
                 break;
@@ -397,161 +393,202 @@ alc_f32_kernel(F32Params P) {
             // cut into phases spread over all warps (with a per-CTA rotation of
             // roles, so that co-resident CTAs use different sub-partitions).
             const int we = (warp + rot) & (F32_WARPS - 1);  // rotated warp role
-            // R0: contender data: FP64 and FP32 coordinates, response, and the
-            // FP32 column of U that serves as the next Schur pivot if it wins
-            for (int e = tid; e < ncon * p; e += F32_THREADS) {
-                const int w = e / p, i = e - w * p;
-                con_x[(size_t)w * p + i] = load_coord64(a.X, con_row[w], p, i, a.dtype);
-                con_c[(size_t)w * p + i] = Cg[(size_t)i * Npad + con_slot[w]];
-            }
-            for (int e = tid; e < ncon * j; e += F32_THREADS) {
-                const int w = e / j, t = e - w * j;
-                con_u[(size_t)w * ld + t] = U[(size_t)t * Npad + con_slot[w]];
-            }
-            if (fused && tid < ncon) {
-                const int row = con_row[tid];
-                con_y[tid] = a.dtype == LAGP_F64 ? static_cast<const double *>(a.Y)[row]
-                                                 : (double)static_cast<const float *>(a.Y)[row];
-            }
-            __syncthreads();
-            // R1: k_j(x_c) in FP64, (contender, design row) pairs packed over lanes
+            // R1: k_j(x_c) and K(x_c, x) in FP64, (contender, design row) pairs
+            // packed over lanes; coordinates straight from the design
             {
+                const int jp = j + 1;
                 const int te = (tid + 32 * rot) & (F32_THREADS - 1);
-                for (int e = te; e < ncon * j; e += F32_THREADS) {
-                    const int w = e / j, t = e - w * j;
-                    const double *xc = con_x + (size_t)w * p;
-                    const double *xt = xd + (size_t)t * p;
+                for (int e = te; e < ncon * jp; e += F32_THREADS) {
+                    const int w = e / jp, t = e - w * jp;
+                    const int32_t row = crow[w];
+                    const double *xt = t < j ? xd + (size_t)t * p : xq;
                     double s0 = 0.0, s1 = 0.0;
                     int i = 0;
                     for (; i + 2 <= p; i += 2) {
-                        const double d0 = xc[i] - xt[i], d1 = xc[i + 1] - xt[i + 1];
+                        const double d0 = load_coord64(a.X, row, p, i, a.dtype) - xt[i];
+                        const double d1 = load_coord64(a.X, row, p, i + 1, a.dtype) - xt[i + 1];
                         s0 = fma(d0, d0, s0);
                         s1 = fma(d1, d1, s1);
                     }
                     if (i < p) {
-                        const double d0 = xc[i] - xt[i];
+                        const double d0 = load_coord64(a.X, row, p, i, a.dtype) - xt[i];
                         s0 = fma(d0, d0, s0);
                     }
-                    con_k[(size_t)w * ld + t] = exp(-(s0 + s1) * inv_d64);
+                    const double kv = exp64_tang(-(s0 + s1) * inv_d64, etab);
+                    if (t < j) {
+                        con_k[(size_t)w * ld + t] = kv;
+                    } else {
+                        con_kap[w] = kv;
+                        if (fused)
+                            con_y[w] = a.dtype == LAGP_F64 ? static_cast<const double *>(a.Y)[row]
+                                                           : (double)static_cast<const float *>(a.Y)[row];
+                    }
                 }
             }
             __syncthreads();
-            // R2: partial contractions K^{-1} k_j(x_c), each contender's rows
-            // split over wpc warps
-            // warps per contender: the largest power of two with ncon * wpc <= 8,
-            // so that the R2 jobs fit the max(8, tmax) rows of cpart
+            // R2: partial contractions [K^{-1} | a | alpha]^T k_j(x_c), each
+            // contender's rows split over wpc warps.  Warps per contender: the
+            // largest power of two with ncon * wpc <= 8, so that the jobs fit
+            // the max(8, tmax) rows of cpart.
             const int wpc = ncon >= 5 ? 1 : (ncon >= 3 ? 2 : (ncon >= 2 ? 4 : 8));
             if (j > 0) {
-                const int rows = max(F32_WARPS, tmax);  // rows of cpart
-                for (int job = we; job < ncon * wpc && job < rows; job += F32_WARPS) {
+                const int nrows = max(F32_WARPS, tmax);  // rows of cpart
+                for (int job = we; job < ncon * wpc && job < nrows; job += F32_WARPS) {
                     const int w = job / wpc, part = job - w * wpc;
                     const int k0 = part * j / wpc, k1 = (part + 1) * j / wpc;
-                    switch ((j + 31) >> 5) {
-                        case 1: partial_contract<1>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
-                        case 2: partial_contract<2>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
-                        case 3: partial_contract<3>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
-                        default: partial_contract<4>(con_k + (size_t)w * ld, Kinv, ld, k0, k1, j, lane, cpart + (size_t)job * ld); break;
+                    const double *kc = con_k + (size_t)w * ld;
+                    double *out = cpart + (size_t)job * ld;
+                    switch ((jo + 31) >> 5) {
+                        case 1: partial_contract<1>(kc, Kinv, ld, k0, k1, jo, lane, out); break;
+                        case 2: partial_contract<2>(kc, Kinv, ld, k0, k1, jo, lane, out); break;
+                        case 3: partial_contract<3>(kc, Kinv, ld, k0, k1, jo, lane, out); break;
+                        case 4: partial_contract<4>(kc, Kinv, ld, k0, k1, jo, lane, out); break;
+                        default: partial_contract<5>(kc, Kinv, ld, k0, k1, jo, lane, out); break;
                     }
                 }
             }
             __syncthreads();
-            // R3: b = sum of the partials; the dot products k^T b, k(x)^T b and
-            // Y^T b, one warp each
-            {
-                const int ns = fused ? 3 : 2;
-                for (int job = we; job < ncon * ns; job += F32_WARPS) {
-                    const int w = job / ns, sdot = job - w * ns;
-                    const double *v = sdot == 0 ? con_k + (size_t)w * ld : (sdot == 1 ? kx : yd);
-                    double acc = 0.0;
-                    for (int t = lane; t < j; t += 32) {
-                        double bt = 0.0;
-                        for (int q = 0; q < wpc; q++) bt += cpart[(size_t)(w * wpc + q) * ld + t];
-                        if (sdot == 0) con_b[(size_t)w * ld + t] = bt;
-                        acc = fma(v[t], bt, acc);
+            // R3: sum of the partials (fixed pairwise order): b = K^{-1} k,
+            // a^T k, alpha^T k; then k^T b, one warp per contender
+            for (int w = we; w < ncon; w += F32_WARPS) {
+                if (j == 0) {
+                    if (lane == 0) con_quad[w] = con_kxb[w] = con_yb[w] = 0.0;
+                    continue;
+                }
+                const double *P0 = cpart + (size_t)w * wpc * ld;
+                double acc = 0.0;
+                for (int t = lane; t < jo; t += 32) {
+                    double bt;
+                    if (wpc == 1) bt = P0[t];
+                    else if (wpc == 2) bt = P0[t] + P0[ld + t];
+                    else if (wpc == 4) bt = (P0[t] + P0[ld + t]) + (P0[2 * ld + t] + P0[3 * ld + t]);
+                    else
+                        bt = ((P0[t] + P0[ld + t]) + (P0[2 * ld + t] + P0[3 * ld + t])) +
+                             ((P0[4 * ld + t] + P0[5 * ld + t]) + (P0[6 * ld + t] + P0[7 * ld + t]));
+                    if (t < j) {
+                        con_b[(size_t)w * ld + t] = bt;
+                        acc = fma(con_k[(size_t)w * ld + t], bt, acc);
+                    } else if (t == j) {
+                        con_kxb[w] = bt;
+                    } else {
+                        con_yb[w] = bt;
                     }
-                    acc = warp_sum(acc);
-                    if (lane == 0) con_dot[sdot][w] = acc;
                 }
+                acc = warp_sum(acc);
+                if (lane == 0) con_quad[w] = acc;
             }
             __syncthreads();
-            // R4: per-contender scalars of Eqs. (piedef), (dxy), in parallel
-            if (tid < ncon) {
-                const int w = tid;
-                const double quad = j > 0 ? con_dot[0][w] : 0.0, kxb = j > 0 ? con_dot[1][w] : 0.0;
-                const double kap = kap64[con_slot[w]];
-                const double minv = (1.0 + g) - quad;  // m_j^{-1}(x_c)
-                const double m = 1.0 / minv;
-                const double kxg = -m * kxb;           // k_j(x)^T g_j(x_c)
-                const double dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
-                con_minv[w] = minv;
-                con_mu[w] = m;
-                con_kxb[w] = kxb;
-                con_kap[w] = kap;
-                const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
-                con_delta[w] = valid ? dl : -CUDART_INF;
-                con_key[w] = valid ? order_key(dl) : INT64_MIN;
-                if (fused) con_ry[w] = con_y[w] - (j > 0 ? con_dot[2][w] : 0.0);  // y - Y^T K^{-1} k
-                con_err[w] = (j >= a.n0 && minv > 0.0 && dl > 0.0)
-                                 ? fabsf(con_s32[w] / (float)dl - 1.f) : 0.f;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int wb = 0;
-                float e = 0.f;
-                for (int w = 0; w < ncon; w++) {
-                    if (w > 0 && (con_key[w] > con_key[wb] ||
-                                  (con_key[w] == con_key[wb] && con_row[w] < con_row[wb])))
-                        wb = w;
-                    e = fmaxf(e, con_err[w]);
+            // R4: per-contender scalars of Eqs. (piedef), (dxy) in the lanes of
+            // warp 0, the winner (largest FP64 value, ties to the lower row),
+            // and mu b of the winner for the update
+            if (warp == 0) {
+                long long key = INT64_MIN;
+                int row = INT32_MAX;
+                float err = 0.f;
+                double m = 0.0, kxb = 0.0, kap = 0.0, ry = 0.0, dl = 0.0;
+                if (lane < ncon) {
+                    const double quad = con_quad[lane];
+                    kxb = con_kxb[lane];
+                    kap = con_kap[lane];
+                    const double minv = onepg - quad;  // m_j^{-1}(x_c)
+                    m = 1.0 / minv;
+                    const double kxg = -m * kxb;       // k_j(x)^T g_j(x_c)
+                    dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
+                    const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
+                    key = valid ? order_key(dl) : INT64_MIN;
+                    row = crow[lane];
+                    if (fused) ry = con_y[lane] - con_yb[lane];  // y - Y^T K^{-1} k
+                    err = (j >= a.n0 && minv > 0.0 && dl > 0.0) ? fabsf(cs32[lane] / (float)dl - 1.f) : 0.f;
                 }
-                if (j >= a.n0) s_err = fmaxf(ERR_DECAY * s_err, e);
-                s_win = wb;
-                if (con_key[wb] == INT64_MIN) s_bad = LAGP_ENOTPD;
+                int wl = lane;
+                long long bk = key;
+                int brow = row;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long ok = __shfl_xor_sync(LAGP_FULL_MASK, bk, o);
+                    const int orow = __shfl_xor_sync(LAGP_FULL_MASK, brow, o);
+                    const int owl = __shfl_xor_sync(LAGP_FULL_MASK, wl, o);
+                    if (ok > bk || (ok == bk && orow < brow)) {
+                        bk = ok;
+                        brow = orow;
+                        wl = owl;
+                    }
+                    err = fmaxf(err, __shfl_xor_sync(LAGP_FULL_MASK, err, o));
+                }
+                const double mu = __shfl_sync(LAGP_FULL_MASK, m, wl);
+                const double *b = con_b + (size_t)wl * ld;
+                for (int t = lane; t < j; t += 32) mb[t] = mu * b[t];
+                if (lane == wl) {
+                    s_wl = wl;
+                    s_mu = m;
+                    s_kap = kap;
+                    s_kxb = kxb;
+                    s_ex = m * (kap - kxb);  // new entry of a = K^{-1} k(x)
+                    s_ry = ry;
+                    s_dl = dl;
+                    if (j >= a.n0) s_err = fmaxf(ERR_DECAY * s_err, err);
+                    if (key == INT64_MIN) s_bad = LAGP_ENOTPD;
+                    s_work[1] += (unsigned long long)ncon;
+                    s_work[2] += (unsigned long long)ncon * j;
+                    s_work[3] += (unsigned long long)ncon * j * j;
+                }
             }
             __syncthreads();
             if (s_bad != LAGP_OK) {
                 status = s_bad;
                 break;
             }
-            // ---------------- FP64 partitioned-inverse update (Sec. 2.2)
-            const int wb = s_win, cstar = con_slot[wb];
+            // ---------------- FP64 partitioned-inverse update (Sec. 2.2) of K^{-1}
+            // and of the vectors a = K^{-1} k(x), alpha = K^{-1} Y beside it
+            const int wl = s_wl, cstar = cslot[wl], rstar = crow[wl];
             {
-                const double mu = con_mu[wb];
-                const double *b = con_b + (size_t)wb * ld;
-                // lower triangle with its mirror: j(j+1)/2 FMAs
+                // the winner's U column, FP32 and FP64 coordinates (next pivot)
+                for (int t = tid; t < j; t += F32_THREADS) w_u[t] = U[(size_t)t * Npad + cstar];
+                for (int i = tid; i < p; i += F32_THREADS) {
+                    w_c[i] = Cg[(size_t)i * Npad + cstar];
+                    xd[(size_t)j * p + i] = load_coord64(a.X, rstar, p, i, a.dtype);
+                }
+                const double *b = con_b + (size_t)wl * ld;
+                // lower triangle with its mirror: K^{-1} += (mu b) b^T
                 for (int e = tid; e < j * (j + 1) / 2; e += F32_THREADS) {
                     int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
                     while ((r + 1) * (r + 2) / 2 <= e) r++;
                     while (r * (r + 1) / 2 > e) r--;
                     const int c = e - r * (r + 1) / 2;
-                    const double val = fma(mu * b[r], b[c], Kinv[(size_t)r * ld + c]);
+                    const double val = fma(mb[r], b[c], Kinv[(size_t)r * ld + c]);
                     Kinv[(size_t)r * ld + c] = val;
                     Kinv[(size_t)c * ld + r] = val;
                 }
-                const double ry = fused ? con_ry[wb] : 0.0;
+                const double ex = s_ex, ry = s_ry;
                 for (int t = tid; t < j; t += F32_THREADS) {
-                    double gt = -mu * b[t];
-                    Kinv[(size_t)t * ld + j] = gt;
+                    double *Kt = Kinv + (size_t)t * ld;
+                    const double a_old = Kt[j];
+                    const double al_old = fused ? Kt[j + 1] : 0.0;
+                    const double gt = -mb[t];
+                    Kt[j] = gt;
                     Kinv[(size_t)j * ld + t] = gt;
-                    if (fused) alpha[t] = fma(-mu * ry, b[t], alpha[t]);
+                    Kt[j + 1] = fma(-ex, b[t], a_old);          // a - e_x b
+                    if (fused) Kt[j + 2] = fma(-ry, mb[t], al_old);  // alpha - mu r_y b
                 }
                 if (tid == 0) {
+                    const double mu = s_mu;
+                    double *Kj = Kinv + (size_t)j * ld;
+                    Kj[j] = mu;
+                    Kj[j + 1] = ex;
                     if (fused) {
                         // Eqs. (predgp), (preds2) carried by the same partitioned
                         // inverse: alpha = K^{-1} Y, psi = Y^T K^{-1} Y,
                         // qx = k(x)^T K^{-1} k(x)
-                        alpha[j] = mu * ry;
-                        yd[j] = con_y[wb];
+                        Kj[j + 2] = mu * ry;
                         s_psi = fma(mu * ry, ry, s_psi);
-                        const double cx = con_kap[wb] - con_kxb[wb];
+                        const double cx = s_kap - s_kxb;
                         s_qx = fma(mu * cx, cx, s_qx);
                     }
-                    Kinv[(size_t)j * ld + j] = mu;
-                    kx[j] = con_kap[wb];
-                    sel[j] = con_row[wb];
-                    if (alc && j >= a.n0) alc[j] = con_delta[wb];
+                    kx[j] = s_kap;
+                    sel[j] = rstar;
+                    if (alc && j >= a.n0) alc[j] = s_dl;
+                    s_total = 0;
                 }
-                for (int i = tid; i < p; i += F32_THREADS) xd[(size_t)j * p + i] = con_x[(size_t)wb * p + i];
             }
             // The FP32 recurrence continues from the pivot's own FP32 state:
             // lambda^2 = v_{x*} and r_{x*}, so that U stays the Cholesky factor
@@ -570,8 +607,6 @@ alc_f32_kernel(F32Params P) {
             {
                 const float inv_lam = rsqrtf(fmaxf(s_vstar, gf));
                 const float wnew = s_covstar * inv_lam;
-                const float *ustar = con_u + (size_t)wb * ld;
-                const float *xs32 = con_c + (size_t)wb * p;
                 float acc[CPT];
 #pragma unroll
                 for (int r = 0; r < CPT; r++) acc[r] = 0.f;
@@ -585,7 +620,7 @@ alc_f32_kernel(F32Params P) {
                     for (int q = 0; q < UNR; q++) load_vec<CPT>(Ub + (size_t)(i + q) * Npad, u[q]);
 #pragma unroll
                     for (int q = 0; q < UNR; q++) {
-                        const float sq = ustar[i + q];
+                        const float sq = w_u[i + q];
 #pragma unroll
                         for (int r = 0; r < CPT; r++) acc[r] = fmaf(u[q][r], sq, acc[r]);
                     }
@@ -593,7 +628,7 @@ alc_f32_kernel(F32Params P) {
                 for (; i < j; i++) {
                     float u0[CPT];
                     load_vec<CPT>(Ub + (size_t)i * Npad, u0);
-                    const float s0 = ustar[i];
+                    const float s0 = w_u[i];
 #pragma unroll
                     for (int r = 0; r < CPT; r++) acc[r] = fmaf(u0[r], s0, acc[r]);
                 }
@@ -603,7 +638,7 @@ alc_f32_kernel(F32Params P) {
                 for (int ii = 0; ii < p; ii++) {
                     float cv[CPT];
                     load_vec<CPT>(Cg + (size_t)ii * Npad + c0, cv);
-                    const float xi = xs32[ii];
+                    const float xi = w_c[ii];
 #pragma unroll
                     for (int r = 0; r < CPT; r++) {
                         float df = cv[r] - xi;
@@ -628,8 +663,6 @@ alc_f32_kernel(F32Params P) {
                 for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(LAGP_FULL_MASK, wm, o));
                 if (lane == 0) w_max[warp] = wm;
             }
-            // the next step's selection starts with a barrier, which orders
-            // column j of U and the per-warp maxima before their readers
         }
         if (status != LAGP_OK) {
             for (int t = tid; t < nmax; t += F32_THREADS) {
@@ -639,19 +672,21 @@ alc_f32_kernel(F32Params P) {
         }
         __syncthreads();
         if (fused && warp == 0) {
+            // mean = k(x)^T alpha; alpha sits in column nm + 1 after the last update
             double m = 0.0;
-            for (int t = lane; t < nm; t += 32) m = fma(kx[t], alpha[t], m);
+            for (int t = lane; t < nm; t += 32) m = fma(kx[t], Kinv[(size_t)t * ld + nm + 1], m);
             m = warp_sum(m);
             if (lane == 0) {
                 const bool ok = status == LAGP_OK;
                 a.mean[loc] = ok ? m : CUDART_NAN;
-                a.s2[loc] = ok ? s_psi * ((1.0 + g) - s_qx) / nm : CUDART_NAN;
+                a.s2[loc] = ok ? s_psi * (onepg - s_qx) / nm : CUDART_NAN;
                 a.df[loc] = ok ? (double)nm : CUDART_NAN;
             }
         }
         if (tid == 0) a.status[loc] = status;
         __syncthreads();
     }
+    if (tid < 4 && P.work) atomicAdd(P.work + tid, s_work[tid]);
 }
 
 template <int CPT>
@@ -659,11 +694,13 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     cudaStream_t st = ctx->stream;
     const int Npad = F32_THREADS * CPT;
     const int tmax = ctx->tuning.rescore_max > 0 ? ctx->tuning.rescore_max : 8;
-    const size_t ld = (size_t)((a.nmax + 31) & ~31);
-    const size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 3 + (size_t)a.nmax * a.p * 8 +
-                        (size_t)a.p * 8 + (size_t)tmax * ld * 8 * 2 + (size_t)tmax * a.p * 8 +
-                        (size_t)tmax * ld * 4 + ((size_t)tmax * a.p + 1) * 4 + 8 +
-                        (size_t)std::max(F32_WARPS, tmax) * ld * 8 + (size_t)Npad * 12 + 64;
+    // dynamic shared memory, in the kernel's order (see alc_f32_kernel)
+    const size_t nmax = (size_t)a.nmax, p = (size_t)a.p;
+    const size_t ld = (nmax + 3) & ~(size_t)1;
+    const size_t union_doubles = std::max((size_t)Npad, (2 * (size_t)tmax + std::max(F32_WARPS, tmax)) * ld);
+    const size_t smem = 8 * ((nmax + 1) * ld + ((nmax + 1) & ~(size_t)1) + nmax * p + ((p + 1) & ~(size_t)1) +
+                             64 + union_doubles) +
+                        4 * (ld + p);
     if (smem > ctx->smem_optin)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, p too large)");
     cudaFuncSetAttribute(alc_f32_kernel<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -675,14 +712,13 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     if (grid > a.M) grid = a.M;
     if (grid < 1) grid = 1;
     const size_t U_floats = (size_t)grid * a.nmax * Npad, C_floats = (size_t)grid * a.p * Npad;
-    const size_t K_doubles = (size_t)grid * Npad;
-    float *U = static_cast<float *>(
-        lagp_ws(ctx, WS_ALC_PANEL, (U_floats + C_floats) * 4 + K_doubles * 8 + 256));
-    int *counter = static_cast<int *>(lagp_ws(ctx, WS_ALC_COUNTER, 256));
-    if (!U || !counter) return LAGP_ENOMEM;
+    float *U = static_cast<float *>(lagp_ws(ctx, WS_ALC_PANEL, (U_floats + C_floats) * 4 + 256));
+    int *counter = nullptr;
+    unsigned long long *work = nullptr;
+    LAGP_TRY(alc_counters(ctx, &counter, &work));
+    if (!U) return LAGP_ENOMEM;
     LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    double *Kw = reinterpret_cast<double *>(U + U_floats + C_floats);  // 8-byte aligned: floats counts are even
-    F32Params P{a, counter, U, U + U_floats, Kw, Npad, tmax, (float)ctx->tuning.rescore_rel};
+    F32Params P{a, counter, work, U, U + U_floats, Npad, tmax, (float)ctx->tuning.rescore_rel};
     alc_f32_kernel<CPT><<<(unsigned)grid, F32_THREADS, smem, st>>>(P);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());

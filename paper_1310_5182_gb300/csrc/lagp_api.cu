@@ -49,6 +49,18 @@ void *lagp_ws(lagp_ctx *ctx, WsSlot slot, size_t bytes) {
     return p;
 }
 
+lagp_status alc_counters(lagp_ctx *ctx, int **counter, unsigned long long **work) {
+    char *base = static_cast<char *>(lagp_ws(ctx, WS_ALC_COUNTER, 256));
+    if (!base) return LAGP_ENOMEM;
+    *counter = reinterpret_cast<int *>(base);
+    *work = reinterpret_cast<unsigned long long *>(base + 128);
+    if (!ctx->work_zeroed) {
+        LAGP_CUDA(ctx, cudaMemsetAsync(*work, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        ctx->work_zeroed = true;
+    }
+    return LAGP_OK;
+}
+
 extern "C" {
 
 const char *lagp_status_string(lagp_status s) {
@@ -123,6 +135,21 @@ lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in) {
 }
 
 int64_t lagp_launch_count(const lagp_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+lagp_status lagp_alc_work(lagp_ctx *ctx, uint64_t *out) {
+    if (!ctx || !out) return LAGP_EINVAL;
+    ctx->err.clear();
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    int *counter = nullptr;
+    unsigned long long *work = nullptr;
+    LAGP_TRY(alc_counters(ctx, &counter, &work));
+    unsigned long long h[4] = {0, 0, 0, 0};
+    LAGP_CUDA(ctx, cudaMemcpyAsync(h, work, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    LAGP_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof h, ctx->stream));
+    LAGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 4; i++) out[i] = h[i];
+    return LAGP_OK;
+}
 
 // --------------------------------------------------------------------- kNN
 

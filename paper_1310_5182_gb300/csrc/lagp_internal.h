@@ -36,6 +36,7 @@ struct lagp_ctx {
     // autotuned resident CTAs per SM, keyed by the ALC problem shape
     std::map<std::string, int> tuned_ctas;
     int tune_override = 0;  // set by the autotuner while it times a candidate
+    bool work_zeroed = false;  // ALC work counters cleared once after allocation
 };
 
 // Shape key of an ALC launch for the autotuner's table.
@@ -43,6 +44,10 @@ std::string alc_shape_key(const char *kernel, int cpt, int nmax, int p, bool fus
 // Resident CTAs per SM for an ALC launch: the autotuner's trial value, the
 // user's tuning, the tuned table, or the kernel's default.
 int alc_ctas_per_sm(lagp_ctx *ctx, const std::string &key, int default_cps);
+
+// The persistent kernels' work counter (offset 0) and the ALC work counters
+// (4 x uint64 at offset 128) of the WS_ALC_COUNTER slot.
+lagp_status alc_counters(lagp_ctx *ctx, int **counter, unsigned long long **work);
 
 // status helpers (lagp_api.cu)
 lagp_status lagp_fail(lagp_ctx *ctx, lagp_status s, const std::string &msg);

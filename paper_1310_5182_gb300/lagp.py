@@ -71,11 +71,13 @@ def _load():
                                   ctypes.c_int, P, P]
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
+    lib.lagp_alc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
-              "lagp_agp"):
+              "lagp_agp", "lagp_alc_work", "lagp_exp64_check"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -200,6 +202,27 @@ def lagp_autotune(X, Xref, idx, n0, n, d, g, prec="f32bulk", Y=None, Nprime=None
 
 def launch_count(device=None) -> int:
     return int(_lib.lagp_launch_count(context(device)))
+
+
+def alc_work(device=None) -> dict:
+    """FP32-bulk search work counters since the last read (then reset):
+    locations, contenders re-scored in FP64 (n_c), sum n_c*j, sum n_c*j^2."""
+    ctx = context(device)
+    out = (ctypes.c_uint64 * 4)()
+    _check(_lib.lagp_alc_work(ctx, out), ctx, "lagp_alc_work")
+    return dict(locations=int(out[0]), rescored=int(out[1]), rescored_j=int(out[2]),
+                rescored_j2=int(out[3]))
+
+
+def exp64_check(a: torch.Tensor):
+    """The library's FP64 exp (Tang's table-driven method) and CUDA's exp at
+    the values of the FP64 device tensor a.  Returns (tang, lib)."""
+    pa = _dev(a, "a", torch.float64)
+    ctx = context(a.device)
+    t, l = torch.empty_like(a), torch.empty_like(a)
+    _check(_lib.lagp_exp64_check(ctx, pa, a.numel(), ctypes.c_void_p(t.data_ptr()),
+                                 ctypes.c_void_p(l.data_ptr())), ctx, "lagp_exp64_check")
+    return t, l
 
 
 def lagp_knn(X: torch.Tensor, Xref: torch.Tensor, Nprime_max: int, Nprime=None):
