@@ -3,21 +3,28 @@
 //
 // Design (GB300): distances are screened in FP32 (74 TFLOP/s) and only the
 // few candidates near the N'-th distance are re-ranked in FP64 (1.2 TFLOP/s).
-//   knn_prep    FP32 copy of an FP64 design, and R = max |coordinate|.
+//   knn_bounds  per-coordinate minimum and maximum of the design and the
+//               reference locations (the centre c and half-width B).
+//   knn_prep    centred FP32 copy of the design, y = fl32(x - c), with the
+//               FP32 squared norm |y|^2 as an extra column.
 //   knn_screen  persistent; 16 queries per CTA, two per warp, sharing every
-//               design tile in shared memory:
+//               design tile in shared memory.  The main launch evaluates
+//               |y_x|^2 + |y_q|^2 - 2 y_x . y_q (one add and p FMAs a pair);
+//               the exact retry the direct sum of squared differences.
 //               (A, B) 2-level histogram (FP32 distance bits [30:21], then
 //               [20:11] inside the boundary bin) over a strided sample of the
 //               design, giving a threshold tau0 expected to bound about 1.3 N'
 //               rows (with stride 1, exactly the N'-th smallest distance);
 //               (C) one pass over the whole design collecting every row below
 //               tau0 widened by a rigorous FP32-vs-FP64 error margin (see
-//               screen_margin) and counting the rows below tau0.  A query
-//               whose count is short of N', or whose buffer overflowed, is
-//               redone by a second launch with stride 1 (the exact method).
+//               expansion_margin, screen_margin) and counting the rows below
+//               tau0.  A query whose count is short of N', or whose buffer
+//               overflowed, is redone by a second launch with stride 1 (the
+//               exact method).
 //   knn_sort    one CTA per query: exact FP64 distances of the collected rows
-//               (separately rounded subtract/multiply/add in coordinate order),
-//               bitonic sort on (d2, row), first N' rows written out.
+//               (separately rounded subtract/multiply/add in coordinate order,
+//               on the original coordinates), bitonic sort on (d2, row), first
+//               N' rows written out.
 // The collected set provably contains the exact FP64 top-N', so the result
 // equals an FP64 sort of all N rows bit for bit.
 #include <cuda_runtime.h>
@@ -36,51 +43,186 @@ constexpr int HB = 1024;              // histogram bins per level (10 bits)
 constexpr int L1_SHIFT = 21;          // level 1: FP32 distance bits [30:21]
 constexpr int L2_SHIFT = 11;          // level 2: bits [20:11] inside the boundary bin
 constexpr uint32_t L2_LOW = (1u << L2_SHIFT) - 1;
-constexpr int TILE_FLOATS = 4096;     // floats of one design tile (tile length x p)
-constexpr int STAGE = TILE_FLOATS / SCREEN_THREADS;  // floats a thread stages per tile
+constexpr int TILE_FLOATS = 4096;     // floats of one design tile (tile length x row stride)
 
-// Design points per tile: a multiple of 32 with tile length x p <= TILE_FLOATS,
-// at most 512.
-__host__ __device__ inline int tile_len(int p) {
-    int t = (TILE_FLOATS / p) & ~31;
+// Floats per centred row: p coordinates and the squared norm, padded to an
+// odd count so that lanes reading consecutive rows of a shared-memory tile
+// hit distinct banks.
+__host__ __device__ inline int row_stride(int p) { return (p + 1) | 1; }
+
+// Design rows per tile: a multiple of 32 with tile length x row stride <=
+// TILE_FLOATS, at most 512.
+__host__ __device__ inline int tile_len(int ps) {
+    int t = (TILE_FLOATS / ps) & ~31;
     return t > 512 ? 512 : (t < 32 ? 32 : t);
 }
+
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// 16-byte asynchronous global-to-shared copy (bypassing L1), and its fences
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 constexpr int CAND_CAP = 8192;        // candidate capacity cap (sort in shared memory)
 constexpr int SORT_THREADS = 256;
 
-__global__ void knn_prep(const double *__restrict__ X, int64_t nX, const double *__restrict__ Xr,
-                         int64_t nR, float *__restrict__ X32, unsigned long long *Rbits) {
-    double mx = 0.0;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nX; i += stride) {
-        double v = X[i];
-        X32[i] = static_cast<float>(v);
-        mx = fmax(mx, fabs(v));
-    }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nR; i += stride)
-        mx = fmax(mx, fabs(Xr[i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(LAGP_FULL_MASK, mx, o));
-    // non-negative doubles order like their bit patterns
-    if ((threadIdx.x & 31) == 0) atomicMax(Rbits, (unsigned long long)__double_as_longlong(mx));
+// Unsigned keys with the order of the doubles (0 below every key), so that
+// zero-initialised buffers work as the identity of atomicMax.
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
 }
 
-// Widened threshold for the collection pass.  With u = 2^-24, coordinates
-// rounded to FP32 with absolute error <= u R (R = 0 for FP32 inputs), FP32
-// differences, squares and sums each rounded once, the FP32 screen value s of
-// a row at exact distance r satisfies
-//     (1-u)^((p+4)/2) (r - 2uR sqrt(p)) <= sqrt(s) <= (1+u)^((p+4)/2) (r + 2uR sqrt(p)).
-// Every row with s <= tau then has r <= r_hi = sqrt(tau) (1-u)^(-(p+4)/2) + 2uR sqrt(p),
+// Per-coordinate bounds of the design and the reference locations:
+// kmax[i] = key of max_i, kmin[i] = ~key of min_i (both maximised).  Eight
+// coordinates per sweep: each thread keeps their bounds in registers over its
+// rows, then warp and block reductions, one atomic per block and coordinate.
+__global__ void knn_bounds(const void *__restrict__ X, int64_t N, const void *__restrict__ Xr,
+                           int64_t M, int p, lagp_dtype dt, unsigned long long *kmax,
+                           unsigned long long *kmin) {
+    __shared__ unsigned long long smax[64], smin[64];
+    for (int i = threadIdx.x; i < p; i += blockDim.x) smax[i] = smin[i] = 0ull;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i0 = 0; i0 < p; i0 += 8) {
+        double lo[8], hi[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            lo[c] = CUDART_INF;
+            hi[c] = -CUDART_INF;
+        }
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N + M; r += stride) {
+            const bool des = r < N;
+            const void *A = des ? X : Xr;
+            const int64_t rr = des ? r : r - N;
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                if (i0 + c >= p) break;
+                const double v = load_coord64(A, rr, p, i0 + c, dt);
+                if (isfinite(v)) {  // a non-finite row only spoils its own distances
+                    lo[c] = fmin(lo[c], v);
+                    hi[c] = fmax(hi[c], v);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[c] = fmin(lo[c], __shfl_xor_sync(LAGP_FULL_MASK, lo[c], o));
+                hi[c] = fmax(hi[c], __shfl_xor_sync(LAGP_FULL_MASK, hi[c], o));
+            }
+            if ((threadIdx.x & 31) == 0 && i0 + c < p && hi[c] >= lo[c]) {
+                atomicMax(&smax[i0 + c], dkey(hi[c]));
+                atomicMax(&smin[i0 + c], ~dkey(lo[c]));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        if (smax[i]) atomicMax(&kmax[i], smax[i]);
+        if (smin[i]) atomicMax(&kmin[i], smin[i]);
+    }
+}
+
+// Centre c_i (midrange of coordinate i) and B = max_i |x_i - c_i| (with a
+// relative slack of 2^-50 for the rounding of c_i), from the bounds of the
+// finite coordinates (a coordinate with none gets c_i = 0, B unchanged).
+__device__ void centre_and_bound(const unsigned long long *kmax, const unsigned long long *kmin,
+                                 int p, double *c, double &B) {
+    double b = 0.0;
+    for (int i = 0; i < p; i++) {
+        if (kmax[i] == 0ull) {  // no finite value in this coordinate
+            c[i] = 0.0;
+            continue;
+        }
+        const double hi = dkey_inv(kmax[i]), lo = dkey_inv(~kmin[i]);
+        const double ci = 0.5 * lo + 0.5 * hi;
+        c[i] = ci;
+        b = fmax(b, fmax(hi - ci, ci - lo) + 0x1p-52 * fmax(fabs(lo), fabs(hi)));
+    }
+    B = b * (1.0 + 0x1p-50);
+}
+
+// Centred FP32 copy of design row r, (y_0 .. y_{p-1}, |y|^2, 0 padding),
+// with y_i = fl32(x_i - c_i) and |y|^2 an FP32 fused multiply-add chain in
+// coordinate order; rows past N are zero.
+__device__ __forceinline__ void centred_row(const void *X, int64_t N, int64_t r, int p, int ps,
+                                            lagp_dtype dt, const double *c, float *out) {
+    float n2 = 0.f;
+    for (int i = 0; i < p; i++) {
+        const float y = r < N ? (float)(load_coord64(X, r, p, i, dt) - c[i]) : 0.f;
+        out[i] = y;
+        n2 = fmaf(y, y, n2);
+    }
+    for (int i = p; i < ps; i++) out[i] = i == p ? n2 : 0.f;
+}
+
+// Y: all rows (Npad of them), Ys: rows 0, s, 2s, ... (nsamp_pad of them;
+// null when s = 1, where the sample is the whole design).
+__global__ void knn_prep(const void *__restrict__ X, int64_t N, int p, lagp_dtype dt,
+                         const unsigned long long *kmax, const unsigned long long *kmin,
+                         float *__restrict__ Y, int64_t Npad, float *__restrict__ Ys,
+                         int64_t nsamp_pad, int64_t sstride) {
+    __shared__ double c[64];
+    __shared__ double sB;
+    if (threadIdx.x == 0) centre_and_bound(kmax, kmin, p, c, sB);
+    __syncthreads();
+    const int ps = row_stride(p);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < Npad; r += stride)
+        centred_row(X, N, r, p, ps, dt, c, Y + r * ps);
+    if (Ys)
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nsamp_pad; r += stride)
+            centred_row(X, N, r * sstride, p, ps, dt, c, Ys + r * ps);
+}
+
+// Widened thresholds for the collection pass.  With u = 2^-24 (widened by
+// 2^-27 for the FP64 centring), centred coordinates rounded to FP32 with
+// absolute error <= u B, the FP32 screen value s of a row relates to its
+// exact distance r as follows.
+//
+// screen_margin (direct form: FP32 differences, squares and sums, each
+// rounded once):
+//     (1-u)^((p+4)/2) (r - 2uB sqrt(p)) <= sqrt(s) <= (1+u)^((p+4)/2) (r + 2uB sqrt(p)).
+// Every row with s <= tau then has r <= r_hi = sqrt(tau) (1-u)^(-(p+4)/2) + 2uB sqrt(p),
 // so the N'-th exact distance is <= r_hi, and every row of the exact top-N' has
-// sqrt(s) <= (r_hi + 2uR sqrt(p)) (1+u)^((p+4)/2).  The final factor covers the
-// rounding of the FP64 reference distances and of this computation.
-__device__ double screen_margin(float tau, int p, double R) {
-    const double u = 5.9604644775390625e-08;  // 2^-24
-    double e2 = 2.0 * u * R * sqrt((double)p);
+// sqrt(s) <= (r_hi + 2uB sqrt(p)) (1+u)^((p+4)/2).
+//
+// expansion_margin (s = max(0, |y_x|^2 + |y_q|^2 - 2 y_x . y_q), every norm
+// and the dot product FMA chains of at most 2p + 4 roundings in all):
+//     |s - |y_q - y_x|^2| <= E = gamma_{2p+4} 4 p B^2,   gamma_k = k u / (1 - k u),
+// and |y_q - y_x| lies within 2uB sqrt(p) of r.  A row with s <= tau then has
+// r <= r_hi = sqrt(tau + E) + 2uB sqrt(p), and every row of the exact top-N'
+// has s <= (r_hi + 2uB sqrt(p))^2 + E.
+//
+// The final factors cover the rounding of the FP64 reference distances (the
+// order is that of the FP64 sums, within a relative 1e-15 of r^2) and of
+// this computation.
+__device__ double screen_margin(float tau, int p, double B) {
+    const double u = 0x1p-24 * (1.0 + 0x1p-27);
+    double e2 = 2.0 * u * B * sqrt((double)p);
     double r = sqrt((double)tau);
-    double r_hi = r * pow(1.0 - u, -0.5 * (p + 4)) + e2;
+    double r_hi = r * pow(1.0 - u, -0.5 * (p + 4)) * (1.0 + 1e-13) + e2;
     double r_col = (r_hi + e2) * pow(1.0 + u, 0.5 * (p + 4));
     return r_col * r_col * (1.0 + 1e-12);
+}
+
+__device__ double expansion_margin(float tau, int p, double B) {
+    const double u = 0x1p-24 * (1.0 + 0x1p-27);
+    const double Bt = B * (1.0 + u);
+    const double e2 = 2.0 * u * B * sqrt((double)p);
+    const double k = 2.0 * p + 4.0;
+    const double E = (k * u / (1.0 - k * u)) * 4.0 * p * Bt * Bt;
+    const double r_hi = sqrt((double)tau + E) * (1.0 + 1e-13) + e2;
+    const double r_col = r_hi + e2;
+    return (r_col * r_col + E) * (1.0 + 1e-12);
 }
 
 // Smallest bin b of the warp's histogram h with cum(h[0..b]) >= target,
@@ -123,38 +265,63 @@ __device__ void find_bin(const uint32_t *h, uint32_t target, int lane, uint32_t 
 
 // One design tile against a warp's QPW queries.  PASS 0: level-1 histogram;
 // PASS 1: level-2 histogram inside the boundary bin; PASS 2: collection.
-template <int P, int PASS>
-__device__ __forceinline__ void screen_tile(const float *t, int TS, int cnt, int lane, int p,
+// Tile row pt holds (y_0 .. y_{p-1}, |y|^2) of a centred design row, with
+// row stride PS.  EXP: s = max(0, |y_x|^2 + |y_q|^2 - 2 y_x . y_q) with
+// qr = -2 y_q and qn = |y_q|^2; otherwise s = sum (y_x - y_q)^2 with qr = y_q.
+template <int P, int PASS, bool EXP>
+__device__ __forceinline__ void screen_tile(const float *t, int ps_rt, int cnt, int lane, int p,
                                             const float (&qr)[QPW][P > 0 ? P : 1],
-                                            const float *qsw, const bool (&ok)[QPW], uint32_t *histw,
+                                            const float (&qn)[QPW], const float *qsw,
+                                            const bool (&ok)[QPW], uint32_t *histw,
                                             const uint32_t (&b1)[QPW], const float (&tau0)[QPW],
                                             const float (&tau2f)[QPW], int32_t *cntw, int32_t *cnt0w,
                                             int32_t *__restrict__ cand, const int64_t (&q)[QPW],
                                             int32_t Cmax, int64_t base) {
+    const int np = P > 0 ? P : p;
+    const int PS = P > 0 ? ((P + 1) | 1) : ps_rt;
     for (int pt = lane; pt < cnt; pt += 32) {
-        float sd[QPW] = {};
+        const float *row = t + pt * PS;
+        float sd[QPW];
+        if constexpr (EXP) {
+            const float xn = row[np];
+#pragma unroll
+            for (int h = 0; h < QPW; h++) sd[h] = xn + qn[h];
+        } else {
+#pragma unroll
+            for (int h = 0; h < QPW; h++) sd[h] = 0.f;
+        }
         if constexpr (P > 0) {
 #pragma unroll
             for (int i = 0; i < P; i++) {
-                const float x = t[i * TS + pt];
+                const float x = row[i];
 #pragma unroll
                 for (int h = 0; h < QPW; h++) {
-                    const float df = x - qr[h][i];
-                    sd[h] = fmaf(df, df, sd[h]);
+                    if constexpr (EXP) {
+                        sd[h] = fmaf(x, qr[h][i], sd[h]);
+                    } else {
+                        const float df = x - qr[h][i];
+                        sd[h] = fmaf(df, df, sd[h]);
+                    }
                 }
             }
         } else {
             for (int i = 0; i < p; i++) {
-                const float x = t[i * TS + pt];
+                const float x = row[i];
 #pragma unroll
                 for (int h = 0; h < QPW; h++) {
-                    const float df = x - qsw[h * p + i];
-                    sd[h] = fmaf(df, df, sd[h]);
+                    const float qv = qsw[h * PS + i];
+                    if constexpr (EXP) {
+                        sd[h] = fmaf(x, -2.f * qv, sd[h]);
+                    } else {
+                        const float df = x - qv;
+                        sd[h] = fmaf(df, df, sd[h]);
+                    }
                 }
             }
         }
 #pragma unroll
         for (int h = 0; h < QPW; h++) {
+            if constexpr (EXP) sd[h] = fmaxf(sd[h], 0.f);
             if constexpr (PASS == 0) {
                 if (ok[h]) atomicAdd(&histw[h * HB + ((__float_as_uint(sd[h]) >> L1_SHIFT) & (HB - 1))], 1u);
             } else if constexpr (PASS == 1) {
@@ -177,27 +344,33 @@ __device__ __forceinline__ void screen_tile(const float *t, int TS, int cnt, int
 //   r = 0, s, 2s, ...; the rtarget-th smallest sampled distance gives tau0
 //   (upper edge of its level-2 bin).  With s = 1 (small designs, and the exact
 //   retry) rtarget = N' and tau0 bounds the N'-th smallest FP32 distance.
-//   Pass C: every row whose FP32 distance is <= screen_margin(tau0) is
+//   Pass C: every row whose FP32 distance is <= the widened threshold is
 //   collected, and the rows <= tau0 are counted; when that count reaches N'
-//   the collected set provably holds the exact FP64 top N' (see
-//   screen_margin).  Otherwise (a sample that underestimated the threshold)
-//   or when the buffer overflows, the query is flagged for the exact retry.
-template <int P>
+//   the collected set provably holds the exact FP64 top N' (see the margin
+//   functions).  Otherwise (a sample that underestimated the threshold) or
+//   when the buffer overflows, the query is flagged for the exact retry.
+template <int P, bool EXP>
 __global__ void __launch_bounds__(SCREEN_THREADS, 2)
-knn_screen(const float *__restrict__ X32, int64_t N, int p, const void *__restrict__ Xref,
+knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t N, int p,
+           const void *__restrict__ Xref,
            lagp_dtype dt, int64_t M, const int32_t *__restrict__ Np, int32_t Npmax,
-           const unsigned long long *__restrict__ Rbits, int32_t *__restrict__ cand, int32_t Cmax,
-           int32_t *__restrict__ cand_count, int32_t *__restrict__ status, int64_t stride,
-           int32_t *__restrict__ retry, int retry_pass, int *__restrict__ counter) {
+           const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
+           int32_t *__restrict__ cand, int32_t Cmax, int32_t *__restrict__ cand_count,
+           int32_t *__restrict__ status, int64_t stride, int32_t *__restrict__ retry, int retry_pass,
+           int *__restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TT = tile_len(p), TS = TT + 1;  // tile length and padded stride
+    const int pp = row_stride(p);              // floats per centred row (coordinates, norm, pad)
+    const int TT = tile_len(pp);               // rows per tile
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);   // QB x HB
-    float *tiles = reinterpret_cast<float *>(hist + QB * HB);  // 2 x p x TS
-    float *qs = tiles + 2 * (size_t)p * TS;                      // QB x p
+    float *tiles = reinterpret_cast<float *>(hist + QB * HB);  // 2 x TT x pp, 16-byte aligned
+    float *qs = tiles + 2 * (size_t)TT * pp;                     // QB x pp: centred queries
     __shared__ int32_t s_count[QB], s_count0[QB];
     __shared__ int64_t s_blk;
+    __shared__ double s_c[64], s_B;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double R = __longlong_as_double((long long)*Rbits);
+    if (threadIdx.x == 0) centre_and_bound(kmax, kmin, p, s_c, s_B);
+    __syncthreads();
+    const double B = s_B;
     const int64_t nsamp = (N + stride - 1) / stride;
 
     for (;;) {
@@ -222,17 +395,32 @@ knn_screen(const float *__restrict__ X32, int64_t N, int p, const void *__restri
             mine_any |= ok[h];
             rtarget[h] = stride == 1 ? k[h]
                                      : (int)min((int64_t)((13 * (int64_t)k[h] + 10 * stride - 1) / (10 * stride)) + 16, nsamp);
-            for (int i = lane; i < p; i += 32) qs[ql * p + i] = active[h] ? load_coord32(Xref, q[h], p, i, dt) : 0.f;
+            if (lane == 0) {
+                float n2 = 0.f;
+                for (int i = 0; i < p; i++) {
+                    const float y = active[h] ? (float)(load_coord64(Xref, q[h], p, i, dt) - s_c[i]) : 0.f;
+                    qs[ql * pp + i] = y;
+                    n2 = fmaf(y, y, n2);
+                }
+                qs[ql * pp + p] = n2;
+                for (int i = p + 1; i < pp; i++) qs[ql * pp + i] = 0.f;
+            }
             for (int b = lane; b < HB; b += 32) hist[ql * HB + b] = 0;
             if (lane == 0) s_count[ql] = s_count0[ql] = 0;
         }
         if (!__syncthreads_or(mine_any)) continue;  // nothing to do in this block
         float qr[QPW][P > 0 ? P : 1] = {};
-        if constexpr (P > 0) {
+        float qn[QPW] = {};
 #pragma unroll
-            for (int h = 0; h < QPW; h++)
+        for (int h = 0; h < QPW; h++) {
+            qn[h] = qs[(w * QPW + h) * pp + p];
+            if constexpr (P > 0) {
 #pragma unroll
-                for (int i = 0; i < P; i++) qr[h][i] = qs[(w * QPW + h) * p + i];
+                for (int i = 0; i < P; i++) {
+                    const float y = qs[(w * QPW + h) * pp + i];
+                    qr[h][i] = EXP ? -2.f * y : y;
+                }
+            }
         }
 
         uint32_t b1[QPW] = {}, before[QPW] = {};
@@ -241,58 +429,43 @@ knn_screen(const float *__restrict__ X32, int64_t N, int p, const void *__restri
         // in FP32 (an FP64 compare per point would occupy the slow FP64 unit)
         float tau0[QPW] = {}, tau2f[QPW] = {};
         for (int pass = 0; pass < 3; pass++) {
-            const int64_t rstride = pass < 2 ? stride : 1;  // passes A, B: sampled rows
+            // passes A, B: the sampled rows (contiguous in Ys); C: all rows
+            const float *src = pass < 2 ? Ys : Y32;
             const int64_t nrows = pass < 2 ? nsamp : N;
             const int64_t ntiles = (nrows + TT - 1) / TT;
-            float stage[STAGE];
-            auto load_stage = [&](int64_t tile) {
+            // tile `tile` into buffer `buf`: its rows rounded up to a multiple of
+            // 4 (zero rows past the end of the padded copies), 16 bytes a copy
+            auto issue = [&](int64_t tile, int buf) {
                 const int64_t base = tile * TT;
-                const int cnt = (int)min((int64_t)TT, nrows - base);
-#pragma unroll
-                for (int u = 0; u < STAGE; u++) {
-                    const int e = threadIdx.x + u * SCREEN_THREADS;
-                    if (e < cnt * p) {
-                        const int pt = (P > 0) ? e / P : e / p, i = e - pt * p;
-                        stage[u] = X32[(base + pt) * rstride * p + i];
-                    } else {
-                        stage[u] = 0.f;
-                    }
-                }
+                const int cnt4 = (int)round_up(min((int64_t)TT, nrows - base), 4);
+                const int nchunk = cnt4 * pp / 4;
+                const float *g = src + base * pp;
+                float *t = tiles + (size_t)buf * TT * pp;
+                for (int e = threadIdx.x; e < nchunk; e += SCREEN_THREADS) cp_async16(t + 4 * e, g + 4 * e);
+                cp_async_commit();
             };
-            auto store_stage = [&](int buf) {
-                float *t = tiles + (size_t)buf * p * TS;
-#pragma unroll
-                for (int u = 0; u < STAGE; u++) {
-                    const int e = threadIdx.x + u * SCREEN_THREADS;
-                    if (e < TT * p) {
-                        const int pt = (P > 0) ? e / P : e / p, i = e - pt * p;
-                        t[i * TS + pt] = stage[u];
-                    }
-                }
-            };
-            load_stage(0);
-            store_stage(0);
+            issue(0, 0);
+            cp_async_wait_all();
             __syncthreads();
             for (int64_t tile = 0; tile < ntiles; tile++) {
                 const int buf = (int)(tile & 1);
-                if (tile + 1 < ntiles) load_stage(tile + 1);  // in flight during the screen
+                if (tile + 1 < ntiles) issue(tile + 1, buf ^ 1);  // in flight during the screen
                 const int64_t base = tile * TT;
                 const int cnt = (int)min((int64_t)TT, nrows - base);
-                const float *t = tiles + (size_t)buf * p * TS;
+                const float *t = tiles + (size_t)buf * TT * pp;
+                const float *qsw = qs + w * QPW * pp;
+                uint32_t *histw = hist + w * QPW * HB;
                 if (pass == 0)
-                    screen_tile<P, 0>(t, TS, cnt, lane, p, qr, qs + w * QPW * p, ok, hist + w * QPW * HB,
-                                      b1, tau0, tau2f, s_count + w * QPW, s_count0 + w * QPW, cand, q,
-                                      Cmax, base);
+                    screen_tile<P, 0, EXP>(t, pp, cnt, lane, p, qr, qn, qsw, ok, histw, b1, tau0, tau2f,
+                                           s_count + w * QPW, s_count0 + w * QPW, cand, q, Cmax, base);
                 else if (pass == 1)
-                    screen_tile<P, 1>(t, TS, cnt, lane, p, qr, qs + w * QPW * p, ok, hist + w * QPW * HB,
-                                      b1, tau0, tau2f, s_count + w * QPW, s_count0 + w * QPW, cand, q,
-                                      Cmax, base);
+                    screen_tile<P, 1, EXP>(t, pp, cnt, lane, p, qr, qn, qsw, ok, histw, b1, tau0, tau2f,
+                                           s_count + w * QPW, s_count0 + w * QPW, cand, q, Cmax, base);
                 else
-                    screen_tile<P, 2>(t, TS, cnt, lane, p, qr, qs + w * QPW * p, ok, hist + w * QPW * HB,
-                                      b1, tau0, tau2f, s_count + w * QPW, s_count0 + w * QPW, cand, q,
-                                      Cmax, base);
-                __syncthreads();  // every warp is done with the other buffer
-                if (tile + 1 < ntiles) store_stage(buf ^ 1);
+                    screen_tile<P, 2, EXP>(t, pp, cnt, lane, p, qr, qn, qsw, ok, histw, b1, tau0, tau2f,
+                                           s_count + w * QPW, s_count0 + w * QPW, cand, q, Cmax, base);
+                // the next tile has landed and every warp is done with this one
+                cp_async_wait_all();
                 __syncthreads();
             }
 #pragma unroll
@@ -307,7 +480,8 @@ knn_screen(const float *__restrict__ X32, int64_t N, int p, const void *__restri
                     uint32_t b2, before2;
                     find_bin(hh, (uint32_t)rtarget[h] - before[h], lane, b2, before2);
                     tau0[h] = __uint_as_float((b1[h] << L1_SHIFT) | (b2 << L2_SHIFT) | L2_LOW);
-                    tau2f[h] = __double2float_rd(screen_margin(tau0[h], p, R));
+                    tau2f[h] = __double2float_rd(EXP ? expansion_margin(tau0[h], p, B)
+                                                     : screen_margin(tau0[h], p, B));
                 }
                 __syncwarp();
             }
@@ -400,16 +574,22 @@ knn_sort(const void *__restrict__ X, int p, lagp_dtype dt, const void *__restric
 }
 
 template <int P>
-void launch_screen(dim3 grid, size_t smem, cudaStream_t st, const float *X32, int64_t N, int p,
+void launch_screen(dim3 grid, size_t smem, cudaStream_t st, const float *Y32, const float *Ys,
+                   int64_t N, int p,
                    const void *Xref, lagp_dtype dt, int64_t M, const int32_t *Np, int32_t Npmax,
-                   const unsigned long long *Rb, int32_t *cand, int32_t Cmax, int32_t *cc,
-                   int32_t *status, int64_t stride, int32_t *retry, int *counters) {
-    cudaFuncSetAttribute(knn_screen<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // sampled threshold, then the exact retry of the flagged queries
-    knn_screen<P><<<grid, SCREEN_THREADS, smem, st>>>(X32, N, p, Xref, dt, M, Np, Npmax, Rb, cand,
-                                                      Cmax, cc, status, stride, retry, 0, counters);
-    knn_screen<P><<<grid, SCREEN_THREADS, smem, st>>>(X32, N, p, Xref, dt, M, Np, Npmax, Rb, cand,
-                                                      Cmax, cc, status, 1, retry, 1, counters + 1);
+                   const unsigned long long *kmax, const unsigned long long *kmin, int32_t *cand,
+                   int32_t Cmax, int32_t *cc, int32_t *status, int64_t stride, int32_t *retry,
+                   int *counters) {
+    cudaFuncSetAttribute(knn_screen<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(knn_screen<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // sampled threshold on the norm expansion, then the exact retry of the
+    // flagged queries on the direct form
+    knn_screen<P, true><<<grid, SCREEN_THREADS, smem, st>>>(Y32, Ys, N, p, Xref, dt, M, Np, Npmax, kmax, kmin,
+                                                            cand, Cmax, cc, status, stride, retry, 0,
+                                                            counters);
+    knn_screen<P, false><<<grid, SCREEN_THREADS, smem, st>>>(Y32, Y32, N, p, Xref, dt, M, Np, Npmax, kmax,
+                                                             kmin, cand, Cmax, cc, status, 1, retry, 1,
+                                                             counters + 1);
 }
 
 }  // namespace
@@ -419,41 +599,41 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
                        int32_t *idx, int32_t *status) {
     cudaStream_t st = ctx->stream;
     const int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
-    // meta: R bits (8 bytes) and two block counters, then per-query candidate
-    // counts and retry flags
-    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, 256 + (size_t)M * 8));
+    // meta: two block counters (offset 64), the coordinate bounds (offsets 256
+    // and 768, 64 keys each), then per-query candidate counts and retry flags
+    constexpr size_t META_HEAD = 1280;
+    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
     int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
-    if (!meta || !cand) return LAGP_ENOMEM;
-    unsigned long long *Rbits = reinterpret_cast<unsigned long long *>(meta);
-    int32_t *cc = reinterpret_cast<int32_t *>(meta + 256);
-    int32_t *retry = cc + M;
+    // sample stride: about 8 N' sampled rows per candidate set, 1 (exact) for small designs
+    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(64, N / (8 * (int64_t)Npmax)));
+    const int pp = row_stride(p);
+    const int64_t Npad = round_up(N, 32), nsamp = (N + stride - 1) / stride;
+    const int64_t nsamp_pad = stride > 1 ? round_up(nsamp, 32) : 0;
+    float *Y32 = static_cast<float *>(lagp_ws(ctx, WS_KNN_X32, (size_t)(Npad + nsamp_pad) * pp * 4));
+    if (!meta || !cand || !Y32) return LAGP_ENOMEM;
+    float *Ys = stride > 1 ? Y32 + Npad * pp : Y32;
     int *counters = reinterpret_cast<int *>(meta + 64);
-    LAGP_CUDA(ctx, cudaMemsetAsync(meta, 0, 256, st));
-    const float *X32;
-    if (dtype == LAGP_F64) {
-        float *x32 = static_cast<float *>(lagp_ws(ctx, WS_KNN_X32, (size_t)N * p * 4));
-        if (!x32) return LAGP_ENOMEM;
-        int blocks = ctx->num_sms * 4;
-        knn_prep<<<blocks, 256, 0, st>>>(static_cast<const double *>(X), N * p,
-                                         static_cast<const double *>(Xref), M * p, x32, Rbits);
-        ctx->launches++;
-        X32 = x32;
-    } else {
-        X32 = static_cast<const float *>(X);  // FP32 inputs: exact, R term not needed
-    }
+    unsigned long long *kmax = reinterpret_cast<unsigned long long *>(meta + 256);
+    unsigned long long *kmin = reinterpret_cast<unsigned long long *>(meta + 768);
+    int32_t *cc = reinterpret_cast<int32_t *>(meta + META_HEAD);
+    int32_t *retry = cc + M;
+    LAGP_CUDA(ctx, cudaMemsetAsync(meta, 0, META_HEAD, st));
+    const int blocks = ctx->num_sms * 4;
+    knn_bounds<<<blocks, 256, 0, st>>>(X, N, Xref, M, p, dtype, kmax, kmin);
+    knn_prep<<<blocks, 256, 0, st>>>(X, N, p, dtype, kmax, kmin, Y32, Npad, stride > 1 ? Ys : nullptr,
+                                     nsamp_pad, stride);
+    ctx->launches += 2;
     LAGP_CUDA(ctx, cudaGetLastError());
 
-    size_t smem = (size_t)QB * HB * 4 + 2 * (size_t)p * (tile_len(p) + 1) * 4 + (size_t)QB * p * 4;
+    size_t smem = (size_t)QB * HB * 4 + 2 * (size_t)tile_len(pp) * pp * 4 + (size_t)QB * pp * 4;
     // persistent grid: two CTAs per SM, blocks of QB queries from a counter
     const int64_t nblk = (M + QB - 1) / QB;
     dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)ctx->num_sms * 2));
-    // sample stride: about 8 N' sampled rows per candidate set, 1 (exact) for small designs
-    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(64, N / (8 * (int64_t)Npmax)));
     switch (p) {
-        case 2: launch_screen<2>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
-        case 3: launch_screen<3>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
-        case 8: launch_screen<8>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
-        default: launch_screen<0>(grid, smem, st, X32, N, p, Xref, dtype, M, Np, Npmax, Rbits, cand, Cmax, cc, status, stride, retry, counters); break;
+        case 2: launch_screen<2>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
+        case 3: launch_screen<3>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
+        case 8: launch_screen<8>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
+        default: launch_screen<0>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
     }
     ctx->launches += 2;
     LAGP_CUDA(ctx, cudaGetLastError());

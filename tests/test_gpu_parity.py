@@ -104,7 +104,8 @@ def compare_selection(gpu_sel, ref, n_arr, n0, g, gap_rel=NEAR_TIE):
 
 # ------------------------------------------------------------------ kNN (a1)
 
-@pytest.mark.parametrize("case", ["toy2d_full", "borehole8d", "slab3d_f32", "ragged", "lattice_ties"])
+@pytest.mark.parametrize("case", ["toy2d_full", "borehole8d", "slab3d_f32", "ragged", "lattice_ties",
+                                  "offset_small_spread", "far_clusters"])
 def test_knn_bit_exact(L, O, case):
     rng = np.random.default_rng(21)
     Np_arr = None
@@ -123,6 +124,15 @@ def test_knn_bit_exact(L, O, case):
         Xr = rng.uniform(0, 1, (29, 8))
         Np_arr = rng.integers(1, 513, 29).astype(np.int32)
         Npm = 512
+    elif case == "offset_small_spread":  # coordinates ~1e4 apart by ~1e-2: centring matters
+        X = 1e4 + 1e-2 * rng.uniform(0, 1, (20_000, 3))
+        Xr = 1e4 + 1e-2 * rng.uniform(0, 1, (31, 3))
+        Npm = 400
+    elif case == "far_clusters":      # tight clusters far apart: wide expansion margin, exact retry
+        centres = rng.uniform(0, 100, (5, 3))
+        X = np.concatenate([c + 1e-3 * rng.standard_normal((2_000, 3)) for c in centres])
+        Xr = np.concatenate([c + 1e-3 * rng.standard_normal((6, 3)) for c in centres])
+        Npm = 500
     else:                             # a lattice: many exact distance ties
         g = np.arange(40, dtype=np.float64)
         X = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
