@@ -267,7 +267,8 @@ __device__ void find_bin(const uint32_t *h, uint32_t target, int lane, uint32_t 
 // PASS 1: level-2 histogram inside the boundary bin; PASS 2: collection.
 // Tile row pt holds (y_0 .. y_{p-1}, |y|^2) of a centred design row, with
 // row stride PS.  EXP: s = max(0, |y_x|^2 + |y_q|^2 - 2 y_x . y_q) with
-// qr = -2 y_q and qn = |y_q|^2; otherwise s = sum (y_x - y_q)^2 with qr = y_q.
+// qr = -2 y_q and qn = |y_q|^2 (negative values, from rounding, clamped to 0);
+// otherwise s = sum (y_x - y_q)^2 with qr = y_q.
 template <int P, int PASS, bool EXP>
 __device__ __forceinline__ void screen_tile(const float *t, int ps_rt, int cnt, int lane, int p,
                                             const float (&qr)[QPW][P > 0 ? P : 1],
@@ -321,7 +322,7 @@ __device__ __forceinline__ void screen_tile(const float *t, int ps_rt, int cnt, 
         }
 #pragma unroll
         for (int h = 0; h < QPW; h++) {
-            if constexpr (EXP) sd[h] = fmaxf(sd[h], 0.f);
+            if constexpr (EXP) sd[h] = sd[h] < 0.f ? 0.f : sd[h];  // keeps NaN
             if constexpr (PASS == 0) {
                 if (ok[h]) atomicAdd(&histw[h * HB + ((__float_as_uint(sd[h]) >> L1_SHIFT) & (HB - 1))], 1u);
             } else if constexpr (PASS == 1) {
@@ -509,15 +510,66 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
     }
 }
 
-__device__ __forceinline__ bool key_less(unsigned long long ka, int32_t ra, unsigned long long kb,
-                                         int32_t rb) {
-    return ka < kb || (ka == kb && ra < rb);
+// Block-wide exclusive prefix sum of one int per thread (SORT_THREADS
+// threads); returns the thread's offset, *total the sum.
+__device__ int block_excl_scan(int v, int *wsum, int *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(LAGP_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int i = 0; i < SORT_THREADS / 32; i++) {
+        off += i < w ? wsum[i] : 0;
+        tot += wsum[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return off + incl - v;
 }
 
+// Bound Delta on |s - r^2| for the direct-form FP32 value s of a row whose
+// FP32 value is at most tau (its exact distance r is then at most
+// Rm = sqrt(tau) (1-u)^(-(p+4)/2) + e2, e2 = 2uB sqrt(p)):
+//     |s - r^2| <= ((1+u)^(p+4) - 1) (Rm + e2)^2 + 2 Rm e2 + e2^2,
+// widened by 1e-6 relative, plus 2e-15 Rm^2 for the rounding of the FP64
+// sums that define the order.  Two rows whose FP32 values differ by more
+// than 2 Delta are in the same order by their FP64 distances, strictly.
+__device__ double tie_bound(float tau, int p, double B) {
+    const double u = 0x1p-24 * (1.0 + 0x1p-27);
+    const double e2 = 2.0 * u * B * sqrt((double)p);
+    const double Rm = sqrt((double)tau) * pow(1.0 - u, -0.5 * (p + 4)) * (1.0 + 1e-13) + e2;
+    const double d0 = (pow(1.0 + u, (double)(p + 4)) - 1.0) * (Rm + e2) * (Rm + e2) + 2.0 * Rm * e2 + e2 * e2;
+    return d0 * (1.0 + 1e-6) + 2e-15 * Rm * Rm;
+}
+
+__device__ __forceinline__ bool pair_less(double da, uint32_t ra, double db, uint32_t rb) {
+    return da < db || (da == db && ra < rb);
+}
+
+// One CTA per query.
+//  (1) direct-form FP32 value s = sum (y_x - y_q)^2 of every collected row;
+//  (2) radix selection of the N'-th smallest, v_k;
+//  (3) survivors: rows with s <= screen_margin(v_k), which hold the exact
+//      FP64 top N' (at least N' collected rows have s <= v_k, so the N'-th
+//      exact distance is bounded as in the screen);
+//  (4) bitonic sort of the survivors on (s, row) as one 64-bit key;
+//  (5) runs of neighbours closer than 2 tie_bound get their exact FP64
+//      distances (separately rounded subtract/multiply/add in coordinate
+//      order, on the original coordinates) and are re-ordered on (d2, row)
+//      within the run; outside the runs the FP32 order is the FP64 order.
+//      A run longer than 32 sends the query to a full FP64 sort instead;
+//  (6) the first N' rows.
 __global__ void __launch_bounds__(SORT_THREADS)
-knn_sort(const void *__restrict__ X, int p, lagp_dtype dt, const void *__restrict__ Xref,
-         int64_t M, const int32_t *__restrict__ Np, int32_t Npmax, const int32_t *__restrict__ cand,
-         const int32_t *__restrict__ cand_count, int32_t Cmax, int32_t *__restrict__ idx) {
+knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_dtype dt,
+         const void *__restrict__ Xref, int64_t M, const int32_t *__restrict__ Np, int32_t Npmax,
+         const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
+         const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_count, int32_t Cmax,
+         int32_t *__restrict__ idx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t q = blockIdx.x;
     const int C = cand_count[q];
@@ -528,49 +580,190 @@ knn_sort(const void *__restrict__ X, int p, lagp_dtype dt, const void *__restric
         return;
     }
     int Cp = 1;
-    while (Cp < C) Cp <<= 1;
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(smem_raw);
-    int32_t *rows = reinterpret_cast<int32_t *>(keys + Cp);
-    double *xq = reinterpret_cast<double *>(rows + Cp + (Cp & 1));
-    for (int i = threadIdx.x; i < p; i += SORT_THREADS) xq[i] = load_coord64(Xref, q, p, i, dt);
-    __syncthreads();
-    for (int e = threadIdx.x; e < Cp; e += SORT_THREADS) {
-        if (e < C) {
-            int32_t r = cand[q * Cmax + e];
-            double s = 0.0;
-            for (int i = 0; i < p; i++) {
-                double diff = __dsub_rn(xq[i], load_coord64(X, r, p, i, dt));
-                s = __dadd_rn(s, __dmul_rn(diff, diff));
-            }
-            keys[e] = (unsigned long long)__double_as_longlong(s);
-            rows[e] = r;
-        } else {
-            keys[e] = ~0ull;
-            rows[e] = INT32_MAX;
+    while (Cp < Cmax) Cp <<= 1;
+    // region 1 (Cp doubles): FP32 keys and rows for steps 1-3, then FP64 keys;
+    // region 2 (Cp words of 64 bits): the survivors' (s, row) keys
+    uint32_t *key32 = reinterpret_cast<uint32_t *>(smem_raw);           // Cmax
+    int32_t *rowA = reinterpret_cast<int32_t *>(key32 + Cp);            // Cmax
+    double *dk = reinterpret_cast<double *>(smem_raw);                  // Cp
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)Cp * 8);  // Cp
+    __shared__ double xq[64], c[64];
+    __shared__ float yq[64];
+    __shared__ double sB, s_delta2;
+    __shared__ uint32_t hist[256];
+    __shared__ int wsum[SORT_THREADS / 32];
+    __shared__ uint32_t s_prefix;
+    __shared__ int s_kk, s_big;
+    __shared__ float s_tauf;
+    __shared__ uint32_t tied[CAND_CAP / 32];
+    const int ps = row_stride(p);
+    if (threadIdx.x == 0) {
+        centre_and_bound(kmax, kmin, p, c, sB);
+        for (int i = 0; i < p; i++) {
+            xq[i] = load_coord64(Xref, q, p, i, dt);
+            yq[i] = (float)(xq[i] - c[i]);
         }
+        s_prefix = 0u;
+        s_kk = k;
+        s_big = 0;
     }
     __syncthreads();
-    // bitonic sort, ascending (key, row)
-    for (int size = 2; size <= Cp; size <<= 1) {
+    // (1) direct-form FP32 values (non-negative floats order like their bits)
+    for (int e = threadIdx.x; e < C; e += SORT_THREADS) {
+        const int32_t r = cand[q * Cmax + e];
+        const float *yr = Y32 + (int64_t)r * ps;
+        float sv = 0.f;
+        for (int i = 0; i < p; i++) {
+            const float df = yr[i] - yq[i];
+            sv = fmaf(df, df, sv);
+        }
+        key32[e] = __float_as_uint(sv);  // NaN keeps the largest keys
+        rowA[e] = r;
+    }
+    // (2) radix selection of the k-th smallest key, 8 bits at a time
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = threadIdx.x; b < 256; b += SORT_THREADS) hist[b] = 0u;
+        __syncthreads();
+        const uint32_t prefix = s_prefix;
+        const uint32_t hmask = shift == 24 ? 0u : (0xffffffffu << (shift + 8));
+        for (int e = threadIdx.x; e < C; e += SORT_THREADS) {
+            const uint32_t kv = key32[e];
+            if ((kv & hmask) == prefix) atomicAdd(&hist[(kv >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const int kk = s_kk;
+            uint32_t sub = 0;
+            for (int b = 0; b < 8; b++) sub += hist[lane * 8 + b];
+            uint32_t incl = sub;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(LAGP_FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const unsigned ball = __ballot_sync(LAGP_FULL_MASK, incl >= (uint32_t)kk);
+            const int L = __ffs(ball) - 1;  // the k-th key is in lane L's bins
+            if (lane == L) {
+                uint32_t cum = incl - sub;
+                int b = 0;
+                for (; b < 7; b++) {
+                    if (cum + hist[lane * 8 + b] >= (uint32_t)kk) break;
+                    cum += hist[lane * 8 + b];
+                }
+                s_prefix = prefix | ((uint32_t)(lane * 8 + b) << shift);
+                s_kk = kk - (int)cum;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float tauf = __double2float_rd(screen_margin(__uint_as_float(s_prefix), p, sB));
+        s_tauf = tauf;
+        s_delta2 = 2.0 * tie_bound(tauf, p, sB);
+    }
+    __syncthreads();
+    const float tauf = s_tauf;
+    // (3) survivors, in candidate order, as (s, row) keys
+    int mine = 0;
+    for (int e = threadIdx.x; e < C; e += SORT_THREADS) mine += __uint_as_float(key32[e]) <= tauf;
+    int S = 0;
+    int pos = block_excl_scan(mine, wsum, &S);
+    for (int e = threadIdx.x; e < C; e += SORT_THREADS)
+        if (__uint_as_float(key32[e]) <= tauf)
+            sk[pos++] = ((unsigned long long)key32[e] << 32) | (uint32_t)rowA[e];
+    int Sp = 1;
+    while (Sp < S) Sp <<= 1;
+    for (int e = S + threadIdx.x; e < Sp; e += SORT_THREADS) sk[e] = ~0ull;
+    __syncthreads();
+    // (4) bitonic sort on (s, row)
+    for (int size = 2; size <= Sp; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int e = threadIdx.x; e < (Cp >> 1); e += SORT_THREADS) {
-                int lo = 2 * e - (e & (stride - 1));
-                int hi = lo + stride;
-                bool up = ((lo & size) == 0);
-                unsigned long long ka = keys[lo], kb = keys[hi];
-                int32_t ra = rows[lo], rb = rows[hi];
-                bool swap = up ? key_less(kb, rb, ka, ra) : key_less(ka, ra, kb, rb);
-                if (swap) {
-                    keys[lo] = kb;
-                    keys[hi] = ka;
-                    rows[lo] = rb;
-                    rows[hi] = ra;
+            for (int e = threadIdx.x; e < (Sp >> 1); e += SORT_THREADS) {
+                const int lo = 2 * e - (e & (stride - 1)), hi = lo + stride;
+                const bool up = ((lo & size) == 0);
+                const unsigned long long ka = sk[lo], kb = sk[hi];
+                if (up ? kb < ka : ka < kb) {
+                    sk[lo] = kb;
+                    sk[hi] = ka;
                 }
             }
             __syncthreads();
         }
     }
-    for (int t = threadIdx.x; t < Npmax; t += SORT_THREADS) out[t] = t < k ? rows[t] : -1;
+    // (5) runs of near-equal FP32 values: FP64 keys, ordered within the run
+    const double d2lim = s_delta2;
+    auto gap_ok = [&](int i) {  // rows i and i + 1 are in a certain FP64 order
+        const double a = (double)__uint_as_float((uint32_t)(sk[i] >> 32));
+        const double b = (double)__uint_as_float((uint32_t)(sk[i + 1] >> 32));
+        return b - a > d2lim;
+    };
+    auto fp64_key = [&](int i) {
+        const int32_t r = (int32_t)(uint32_t)sk[i];
+        double sd = 0.0;
+        for (int t = 0; t < p; t++) {
+            const double diff = __dsub_rn(xq[t], load_coord64(X, r, p, t, dt));
+            sd = __dadd_rn(sd, __dmul_rn(diff, diff));
+        }
+        return sd;
+    };
+    // tie flags first (bit i: rows i and i + 1 need their FP64 order), so that
+    // no run is re-ordered while another thread still reads its FP32 keys
+    for (int w = threadIdx.x; w < (Sp + 31) / 32; w += SORT_THREADS) tied[w] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i + 1 < S; i += SORT_THREADS)
+        if (!gap_ok(i)) atomicOr(&tied[i >> 5], 1u << (i & 31));
+    __syncthreads();
+    auto is_tied = [&](int i) { return (tied[i >> 5] >> (i & 31)) & 1u; };
+    for (int i = threadIdx.x; i < S; i += SORT_THREADS) {
+        if (!is_tied(i) || (i > 0 && is_tied(i - 1))) continue;  // not the start of a run
+        int end = i + 1;  // the run is [i, end]
+        while (is_tied(end) && end - i < 32) end++;
+        if (end - i >= 32) {
+            s_big = 1;
+            continue;
+        }
+        for (int t = i; t <= end; t++) dk[t] = fp64_key(t);
+        for (int t = i + 1; t <= end; t++) {  // insertion sort on (d2, row)
+            const double dv = dk[t];
+            const unsigned long long kv = sk[t];
+            int u = t - 1;
+            while (u >= i && pair_less(dv, (uint32_t)kv, dk[u], (uint32_t)sk[u])) {
+                dk[u + 1] = dk[u];
+                sk[u + 1] = sk[u];
+                u--;
+            }
+            dk[u + 1] = dv;
+            sk[u + 1] = kv;
+        }
+    }
+    __syncthreads();
+    if (s_big) {
+        // a long run: exact FP64 keys for every survivor and a full sort on (d2, row)
+        for (int i = threadIdx.x; i < Sp; i += SORT_THREADS) dk[i] = i < S ? fp64_key(i) : CUDART_INF;
+        __syncthreads();
+        for (int size = 2; size <= Sp; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int e = threadIdx.x; e < (Sp >> 1); e += SORT_THREADS) {
+                    const int lo = 2 * e - (e & (stride - 1)), hi = lo + stride;
+                    const bool up = ((lo & size) == 0);
+                    const double da = dk[lo], db = dk[hi];
+                    const unsigned long long ka = sk[lo], kb = sk[hi];
+                    const bool swap = up ? pair_less(db, (uint32_t)kb, da, (uint32_t)ka)
+                                         : pair_less(da, (uint32_t)ka, db, (uint32_t)kb);
+                    if (swap) {
+                        dk[lo] = db;
+                        dk[hi] = da;
+                        sk[lo] = kb;
+                        sk[hi] = ka;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // (6)
+    for (int t = threadIdx.x; t < Npmax; t += SORT_THREADS) out[t] = t < k ? (int32_t)(uint32_t)sk[t] : -1;
 }
 
 template <int P>
@@ -640,11 +833,11 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
 
     int Cp = 1;
     while (Cp < Cmax) Cp <<= 1;
-    size_t smem_sort = (size_t)Cp * 12 + 8 + (size_t)p * 8 + 16;
+    size_t smem_sort = (size_t)Cp * 16;
     if (smem_sort > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: N' too large for the sort");
     cudaFuncSetAttribute(knn_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sort);
-    knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, p, dtype, Xref, M, Np, Npmax, cand, cc,
-                                                           Cmax, idx);
+    knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Y32, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
+                                                           cand, cc, Cmax, idx);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
     return LAGP_OK;
