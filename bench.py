@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (2-d toy in both precisions, the 1M-point "
+                         "uneven borehole with MLE)")
+    ap.add_argument("--extra", action="store_true",
+                    help="also time the 3-d slab grid and the 4M-point borehole (both with MLE)")
     ap.add_argument("--M", type=int, default=None,
                     help="reference locations per GPU (default: the workload's 10,000; smaller "
                          "values are for profiler captures, not bench lines)")
@@ -210,6 +215,73 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- the other configurations
+
+def config_leg(L, dev, w, prec, steps, warmup, flush=None):
+    """Whole-batch rate of one configuration: kNN, then either the fused
+    search + prediction (fixed d) or search -> Newton MLE of d -> prediction
+    (w.mle set), with per-location n and N' as device arrays."""
+    import torch
+    X, Y, Xr = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.X, w.Y, w.Xref))
+    n_t = torch.from_numpy(w.n).to(dev)
+    Np_t = torch.from_numpy(w.Np).to(dev)
+    Npm, nmax = int(w.Np.max()), int(w.n.max())
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        idx, st = L.lagp_knn(X, Xr, Npm, Nprime=Np_t)
+        if w.mle is None:
+            out = L.lagp_alc_predict(X, Y, Xr, idx, w.n0, n_t, w.d, w.g, prec=prec, Nprime=Np_t,
+                                     n_max=nmax)
+            return out["mean"], [st, out["status"]]
+        s = L.lagp_alc_select(X, Xr, idx, w.n0, n_t, w.d, w.g, prec=prec, Nprime=Np_t, n_max=nmax)
+        m = L.lagp_mle_step(X, Y, s["sel"], n_t, w.d, w.g, *w.mle)
+        pr = L.lagp_predict(X, Y, Xr, s["sel"], n_t, m["d"], w.g)
+        return pr["mean"], [st, s["status"], m["status"], pr["status"]]
+
+    for _ in range(warmup):
+        step()
+    times = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mean, sts = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+    ok = np.all([t.cpu().numpy() == 0 for t in sts], axis=0)
+    mean = mean.cpu().numpy()
+    ms = statistics.mean(times)
+    return {"value": w.M / (ms / 1e3), "unit": "predictions/s", "ms_per_step": ms, "steps": steps,
+            "M": w.M, "N": w.N, "p": w.p, "n": [int(w.n.min()), int(w.n.max())],
+            "Nprime": [int(w.Np.min()), int(w.Np.max())], "dtype": str(w.X.dtype), "prec": prec,
+            "mle": list(w.mle) if w.mle else None, "status_ok_frac": float(ok.mean()),
+            "rmse_vs_truth": float(np.sqrt(np.mean((mean[ok] - w.truth[ok]) ** 2)))}
+
+
+def other_configs(L, dev, args, flush):
+    out = {}
+    w1 = W.c1_toy2d_fp64()
+    for prec in ("f64", "f32bulk"):
+        out[f"toy2d_N10000_M100_n50_Nprime1000_{prec}"] = config_leg(L, dev, w1, prec, 10, 3, flush)
+    w3 = W.c3_borehole_1m_uneven()
+    out["borehole8d_N1000000_M20000_n30-100_Nprime500-2000_mle"] = config_leg(L, dev, w3, "f32bulk", 2, 1,
+                                                                              flush)
+    del w3
+    if args.extra:
+        w4 = W.c4_slab3d()
+        out["slab3d_N500000_grid60x60x56_n60_Nprime1500_mle"] = config_leg(L, dev, w4, "f32bulk", 2, 1,
+                                                                           flush)
+        del w4
+        w5 = W.c5_borehole_4m()
+        out["borehole8d_N4000000_M100000_n50_Nprime2000_mle"] = config_leg(L, dev, w5, "f32bulk", 2, 1,
+                                                                           flush)
+    return out
+
+
 # ------------------------------------------------------------------- ours
 
 def run_ours(args, rank, world, local_rank):
@@ -359,6 +431,9 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": Xh.nbytes + Yh.nbytes + Xrh.nbytes + 2 * M * 4,
                "d2h_bytes_per_step": 4 * M * 8 + 4 * M * 4}
 
+    configs = None
+    if not args.no_configs and world == 1:
+        configs = other_configs(L, dev, args, flush)
     if rank != 0:
         return
     E = work_per_location(n0, n, Np)
@@ -409,6 +484,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
 

@@ -281,17 +281,28 @@ lagp_status lagp_predict_noalloc(lagp_ctx *ctx, const void *X, const void *Y, in
 
 /* --------------------------------------------- whole method, host buffers
  * The multi-stage algorithm of Fig. 1 for every reference location:
- * kNN (a1) -> greedy ALC design at lengthscale d0 (a2..a6) -> optional local
- * MLE of d on that design (a8, when do_mle != 0) -> prediction (a7) with the
- * final d.  All array arguments are HOST pointers; the inputs are copied to
- * the device, and the outputs copied back, inside the call, which returns
+ * kNN (a1) -> greedy ALC design at lengthscale d0 (a2..a6) -> local MLE of d
+ * on that design (a8) -> ... -> prediction (a7).  mle_rounds = 0 predicts on
+ * the design at d0 (no MLE; the prediction is carried by the search itself).
+ * mle_rounds = r >= 1 runs Fig. 1 steps 2-3 r times (step 4: "repeat as
+ * desired"): each round searches the designs at the current per-location d
+ * and then moves d to the MLE on that design, starting from the current d;
+ * the prediction (step 5) uses the last design and estimate.  r = 2 is the
+ * two-stage scheme of Sec. 3.1 (designs re-searched with the local
+ * estimates).  All array arguments are HOST pointers; the inputs are copied
+ * to the device, and the outputs copied back, inside the call, which returns
  * after the outputs are in host memory.
  *   Nprime, n   M per-location values or NULL (all = Nprime_max / n_max)
- *   mean, s2, df, status   M outputs;  d_out  M final lengthscales or NULL */
+ *   mle_rounds  0 .. LAGP_MAX_MLE_ROUNDS; dmin, dmax, max_iter as in
+ *               lagp_mle_step (ignored when mle_rounds = 0)
+ *   mean, s2, df, status   M outputs (status: the first failing stage, in
+ *               the order kNN, each round's search and MLE, prediction)
+ *   d_out  M final lengthscales or NULL */
+#define LAGP_MAX_MLE_ROUNDS 16
 lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
                      lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *Nprime,
                      int32_t Nprime_max, int32_t n0, const int32_t *n, int32_t n_max,
-                     double d0, double g, lagp_precision prec, int32_t do_mle, double dmin,
+                     double d0, double g, lagp_precision prec, int32_t mle_rounds, double dmin,
                      double dmax, int32_t max_iter, double *mean, double *s2, double *df,
                      double *d_out, int32_t *status);
 

@@ -220,19 +220,25 @@ def predict_grad(X, Y, Xref, sel, n, d, g):
     return r
 
 
-def run_pipeline(X, Y, Xref, n0, n, Np, d, g, mle_args=None, Np_arr=None):
-    """kNN -> ALC search -> (MLE) -> predict for every location (FP64)."""
+def run_pipeline(X, Y, Xref, n0, n, Np, d, g, mle_args=None, Np_arr=None, rounds=1):
+    """kNN -> ALC search -> (MLE) -> predict for every location (FP64),
+    Fig. 1.  With mle_args, steps 2-3 (search at the current d, then the MLE
+    of d on that design from the current d) run `rounds` times (step 4);
+    rounds=2 is the two-stage scheme."""
     M = len(Xref)
     n_arr = _per_loc(n, M, np.int32, 0)
     Np_max = int(np.max(Np_arr)) if Np_arr is not None else int(Np)
     idx = knn(X, Xref, Np_max, Np_arr)
-    s = alc_select(X, Xref, idx, n0, n_arr, d, g, Np=Np_arr)
     dd = _per_loc(d, M, np.float64, 0.0)
-    out = dict(idx=idx, sel=s["sel"], alc=s["alc"], sel_status=s["status"])
-    if mle_args is not None:
-        r = mle(X, Y, s["sel"], n_arr, dd, g, *mle_args)
-        dd = r["d"]
-        out["mle"] = r
+    out = dict(idx=idx, rounds=[])
+    for _ in range(rounds if mle_args is not None else 1):
+        s = alc_select(X, Xref, idx, n0, n_arr, dd, g, Np=Np_arr)
+        out.update(sel=s["sel"], alc=s["alc"], sel_status=s["status"])
+        if mle_args is not None:
+            r = mle(X, Y, s["sel"], n_arr, dd, g, *mle_args)
+            out["rounds"].append(dict(sel=s["sel"], d_in=dd, d=r["d"]))
+            dd = r["d"]
+            out["mle"] = r
     out.update(predict(X, Y, Xref, s["sel"], n_arr, dd, g))
     out["d"] = dd
     return out

@@ -302,7 +302,7 @@ lagp_status lagp_predict_grad(lagp_ctx *ctx, const void *X, const void *Y, int64
 lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int32_t p,
                      lagp_dtype dtype, const void *Xref, int64_t M, const int32_t *Nprime,
                      int32_t Nprime_max, int32_t n0, const int32_t *n, int32_t n_max,
-                     double d0, double g, lagp_precision prec, int32_t do_mle, double dmin,
+                     double d0, double g, lagp_precision prec, int32_t mle_rounds, double dmin,
                      double dmax, int32_t max_iter, double *mean, double *s2, double *df,
                      double *d_out, int32_t *status) {
     if (!ctx) return LAGP_EINVAL;
@@ -313,6 +313,8 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
     if (!Y || !Xref || !mean || !s2 || !df || !status)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: NULL required array");
     if (!(d0 > 0.0)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: d0 must be > 0");
+    if (mle_rounds < 0 || mle_rounds > LAGP_MAX_MLE_ROUNDS)
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: mle_rounds must be in [0, 16]");
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
 
     const size_t es = dtype == LAGP_F64 ? 8 : 4;
@@ -321,8 +323,10 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
     size_t oX = 0, oY = oX + al(N * p * es), oR = oY + al(N * es), oNp = oR + al(M * p * es);
     size_t on = oNp + al(M * 4), oIdx = on + al(M * 4), oSel = oIdx + al(M * (size_t)Nprime_max * 4);
     size_t od = oSel + al(M * (size_t)n_max * 4), oMean = od + al(M * 8), oS2 = oMean + al(M * 8);
-    size_t oDf = oS2 + al(M * 8), oSt = oDf + al(M * 8), oSt2 = oSt + al(M * 4), oSt3 = oSt2 + al(M * 4),
-           oSt4 = oSt3 + al(M * 4), total = oSt4 + al(M * 4);
+    // statuses: kNN, then (selection, MLE) per round (one selection without
+    // MLE), then prediction
+    const int nst = 2 + 2 * (mle_rounds > 0 ? mle_rounds : 1);
+    size_t oDf = oS2 + al(M * 8), oSt = oDf + al(M * 8), total = oSt + (size_t)nst * al(M * 4);
     char *base = static_cast<char *>(lagp_ws(ctx, WS_AGP_IO, total));
     if (!base) return LAGP_ENOMEM;
     void *dX = base + oX, *dY = base + oY, *dR = base + oR;
@@ -334,10 +338,7 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
     double *dMean = reinterpret_cast<double *>(base + oMean);
     double *dS2 = reinterpret_cast<double *>(base + oS2);
     double *dDf = reinterpret_cast<double *>(base + oDf);
-    int32_t *dSt = reinterpret_cast<int32_t *>(base + oSt);
-    int32_t *dSt2 = reinterpret_cast<int32_t *>(base + oSt2);
-    int32_t *dSt3 = reinterpret_cast<int32_t *>(base + oSt3);
-    int32_t *dSt4 = reinterpret_cast<int32_t *>(base + oSt4);
+    auto dSt = [&](int i) { return reinterpret_cast<int32_t *>(base + oSt + (size_t)i * al(M * 4)); };
     cudaStream_t st = ctx->stream;
 
     LAGP_CUDA(ctx, cudaMemcpyAsync(dX, X, N * p * es, cudaMemcpyHostToDevice, st));
@@ -351,35 +352,40 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
         LAGP_CUDA(ctx, cudaMemcpyAsync(dd, h.data(), M * 8, cudaMemcpyHostToDevice, st));
         LAGP_CUDA(ctx, cudaStreamSynchronize(st));  // h leaves scope
     }
-    LAGP_TRY(lagp_knn(ctx, dX, N, p, dtype, dR, M, dNp, Nprime_max, dIdx, dSt4));
-    if (do_mle) {
-        // design at d0, MLE of d on that design, prediction with the estimate
-        LAGP_TRY(lagp_alc_select(ctx, dX, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn, n_max,
-                                 dd, g, prec, dSel, nullptr, dSt));
-        LAGP_TRY(lagp_mle_step(ctx, dX, dY, N, p, dtype, M, dSel, dn, n_max, dd, g, dmin, dmax,
-                               max_iter, nullptr, nullptr, nullptr, nullptr, dSt2));
+    LAGP_TRY(lagp_knn(ctx, dX, N, p, dtype, dR, M, dNp, Nprime_max, dIdx, dSt(0)));
+    if (mle_rounds > 0) {
+        // Fig. 1 steps 2-3, repeated (step 4): design at the current d, MLE of
+        // d on that design starting from the current d; then prediction (step
+        // 5) with the last design and estimate
+        for (int r = 0; r < mle_rounds; r++) {
+            LAGP_TRY(lagp_alc_select(ctx, dX, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn, n_max,
+                                     dd, g, prec, dSel, nullptr, dSt(1 + 2 * r)));
+            LAGP_TRY(lagp_mle_step(ctx, dX, dY, N, p, dtype, M, dSel, dn, n_max, dd, g, dmin, dmax,
+                                   max_iter, nullptr, nullptr, nullptr, nullptr, dSt(2 + 2 * r)));
+        }
         LAGP_TRY(lagp_predict(ctx, dX, dY, N, p, dtype, dR, M, dSel, dn, n_max, dd, g, dMean, dS2,
-                              dDf, dSt3));
+                              dDf, dSt(nst - 1)));
     } else {
         // prediction carried by the search itself (one kernel)
         LAGP_TRY(lagp_alc_predict(ctx, dX, dY, N, p, dtype, dR, M, dIdx, dNp, Nprime_max, n0, dn,
-                                  n_max, dd, g, prec, dSel, nullptr, dMean, dS2, dDf, dSt));
-        LAGP_CUDA(ctx, cudaMemsetAsync(dSt2, 0, M * 4, st));
-        LAGP_CUDA(ctx, cudaMemsetAsync(dSt3, 0, M * 4, st));
+                                  n_max, dd, g, prec, dSel, nullptr, dMean, dS2, dDf, dSt(1)));
+        LAGP_CUDA(ctx, cudaMemsetAsync(dSt(2), 0, M * 4, st));
+        LAGP_CUDA(ctx, cudaMemsetAsync(dSt(3), 0, M * 4, st));
     }
     LAGP_CUDA(ctx, cudaMemcpyAsync(mean, dMean, M * 8, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaMemcpyAsync(s2, dS2, M * 8, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaMemcpyAsync(df, dDf, M * 8, cudaMemcpyDeviceToHost, st));
     if (d_out) LAGP_CUDA(ctx, cudaMemcpyAsync(d_out, dd, M * 8, cudaMemcpyDeviceToHost, st));
-    std::vector<int32_t> s1(M), s2v(M), s3(M), s4(M);
-    LAGP_CUDA(ctx, cudaMemcpyAsync(s4.data(), dSt4, M * 4, cudaMemcpyDeviceToHost, st));
-    LAGP_CUDA(ctx, cudaMemcpyAsync(s1.data(), dSt, M * 4, cudaMemcpyDeviceToHost, st));
-    LAGP_CUDA(ctx, cudaMemcpyAsync(s2v.data(), dSt2, M * 4, cudaMemcpyDeviceToHost, st));
-    LAGP_CUDA(ctx, cudaMemcpyAsync(s3.data(), dSt3, M * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> sv((size_t)nst * M);
+    for (int i = 0; i < nst; i++)
+        LAGP_CUDA(ctx, cudaMemcpyAsync(sv.data() + (size_t)i * M, dSt(i), M * 4, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaStreamSynchronize(st));
-    // first failing stage wins: kNN, selection, MLE, prediction
-    for (int64_t m = 0; m < M; m++)
-        status[m] = s4[m] != LAGP_OK ? s4[m] : s1[m] != LAGP_OK ? s1[m] : s2v[m] != LAGP_OK ? s2v[m] : s3[m];
+    // first failing stage wins: kNN, then each round's selection and MLE, then prediction
+    for (int64_t m = 0; m < M; m++) {
+        int32_t v = LAGP_OK;
+        for (int i = 0; i < nst && v == LAGP_OK; i++) v = sv[(size_t)i * M + m];
+        status[m] = v;
+    }
     return LAGP_OK;
 }
 

@@ -380,10 +380,12 @@ def lagp_predict_grad(X, Y, Xref, sel, n, d, g):
     return out
 
 
-def lagp_agp(X, Y, Xref, n0, n, Nprime, d0, g, prec="f32bulk", mle=None, device=0):
+def lagp_agp(X, Y, Xref, n0, n, Nprime, d0, g, prec="f32bulk", mle=None, rounds=1, device=0):
     """The whole method on HOST arrays (numpy or CPU tensors): kNN -> ALC ->
-    optional MLE (mle = (dmin, dmax, max_iter)) -> predict.  Inputs are copied
-    to the GPU and results back inside the call.  Returns numpy arrays."""
+    MLE (when mle = (dmin, dmax, max_iter) is given; search and MLE repeated
+    `rounds` times, rounds=2 being the two-stage scheme) -> predict.  Inputs
+    are copied to the GPU and results back inside the call.  Returns numpy
+    arrays."""
     ctx = context(device)
     X = np.ascontiguousarray(X)
     if X.dtype not in (np.float64, np.float32):
@@ -401,7 +403,7 @@ def lagp_agp(X, Y, Xref, n0, n, Nprime, d0, g, prec="f32bulk", mle=None, device=
     _check(_lib.lagp_agp(ctx, ptr(X), ptr(Y), N, p, LAGP_F64 if X.dtype == np.float64 else LAGP_F32,
                          ptr(Xref), M, ptr(Np_arr), int(Np_arr.max()) if M else 1, int(n0), ptr(n_arr),
                          int(n_arr.max()) if M else int(n0), float(d0), float(g), _PREC[prec],
-                         1 if mle is not None else 0, float(dmin), float(dmax), int(it),
+                         int(rounds) if mle is not None else 0, float(dmin), float(dmax), int(it),
                          ptr(out["mean"]), ptr(out["s2"]), ptr(out["df"]), ptr(out["d"]), ptr(status)),
            ctx, "lagp_agp")
     out["status"] = status

@@ -370,6 +370,40 @@ def test_agp_host_buffers_match_oracle(L, O):
 
 
 @pytest.mark.parametrize("prec", ["f32bulk", "f64"])
+def test_agp_two_stage(L, O, prec):
+    """Fig. 1 step 4 with two rounds: search at d0, MLE, search again at the
+    local estimates, MLE from them, predict.  Each stage is checked against
+    the oracle on the GPU's own inputs to that stage, and the host-buffer
+    entry point must reproduce the device-level composition exactly."""
+    w = W.borehole(seed=33, N=20_000, M=40, n=30, Np=300)
+    mle = (1e-3, 20.0, 10)
+    n0, n, Np, d0, g = 6, 30, 300, 2.0, w.g
+    X, Y, Xr = dev(w.X), dev(w.Y), dev(w.Xref)
+    idx, _ = L.lagp_knn(X, Xr, Np)
+    d = torch.full((w.M,), d0, dtype=torch.float64, device="cuda")
+    for r in range(2):
+        s = L.lagp_alc_select(X, Xr, idx, n0, n, d, g, prec=prec)
+        sel = s["sel"].cpu().numpy()
+        assert (s["status"].cpu().numpy() == 0).all()
+        ref = O.alc_select(w.X, w.Xref, idx.cpu().numpy(), n0, n, d.cpu().numpy(), g, topk=4)
+        div = compare_selection(sel, ref, np.full(w.M, n), n0, g)
+        assert len(div) <= 0.05 * w.M
+        m = L.lagp_mle_step(X, Y, s["sel"], n, d, g, *mle)
+        ref_m = O.mle(w.X, w.Y, sel, n, d.cpu().numpy(), g, *mle)
+        np.testing.assert_allclose(m["d"].cpu().numpy(), ref_m["d"], rtol=1e-6)
+        d = m["d"]
+    pr = L.lagp_predict(X, Y, Xr, s["sel"], n, d, g)
+    ref_p = O.predict(w.X, w.Y, w.Xref, sel, n, d.cpu().numpy(), g)
+    check_pred(pr["mean"].cpu().numpy(), pr["s2"].cpu().numpy(), ref_p, w.X, w.Y, w.Xref, sel,
+               np.full(w.M, n), d.cpu().numpy(), g)
+    out = L.lagp_agp(w.X, w.Y, w.Xref, n0, n, Np, d0, g, prec=prec, mle=mle, rounds=2)
+    assert (out["status"] == 0).all()
+    np.testing.assert_array_equal(out["d"], d.cpu().numpy())
+    np.testing.assert_array_equal(out["mean"], pr["mean"].cpu().numpy())
+    np.testing.assert_array_equal(out["s2"], pr["s2"].cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["f32bulk", "f64"])
 def test_borehole_full_size_sampled(L, O, prec):
     """The full 8-d borehole configuration (N=100,000, M=10,000, (6, 50, 1000),
     d=2, g=1e-6) run whole on the GPU, exactly as the benchmark launches it;
@@ -400,3 +434,36 @@ def test_borehole_full_size_sampled(L, O, prec):
     refp = {k: v[same] for k, v in refp.items()}
     check_pred(pr["mean"].cpu().numpy()[samp][same], pr["s2"].cpu().numpy()[samp][same], refp, w.X,
                w.Y, w.Xref[samp][same], ref["sel"][same], np.full(len(same), 50), 2.0, 1e-6)
+
+
+def test_borehole_1m_uneven_mle_full_size_sampled(L, O):
+    """The 1M-point uneven configuration (N=1,000,000 FP32, M=20,000,
+    n ~ U{30..100}, N' ~ U{500..2000}, Newton MLE of d from 2.0 within
+    [1e-3, 20], <= 10 iterations) run whole on the GPU as the benchmark runs
+    it; sampled locations are checked stage by stage against the oracle on
+    the GPU's own inputs to each stage."""
+    w = W.c3_borehole_1m_uneven()
+    X, Y, Xr = dev(w.X), dev(w.Y), dev(w.Xref)
+    n_t, Np_t = dev(w.n), dev(w.Np)
+    Npm, nmax = int(w.Np.max()), int(w.n.max())
+    idx, st = L.lagp_knn(X, Xr, Npm, Nprime=Np_t)
+    s = L.lagp_alc_select(X, Xr, idx, w.n0, n_t, w.d, w.g, prec="f32bulk", Nprime=Np_t, n_max=nmax)
+    m = L.lagp_mle_step(X, Y, s["sel"], n_t, w.d, w.g, *w.mle)
+    pr = L.lagp_predict(X, Y, Xr, s["sel"], n_t, m["d"], w.g)
+    torch.cuda.synchronize()
+    for t in (st, s["status"], m["status"], pr["status"]):
+        assert (t.cpu().numpy() == 0).all()
+    samp = np.random.default_rng(41).choice(w.M, 8, replace=False)
+    n_s, Np_s = w.n[samp], w.Np[samp]
+    ref_idx = O.knn(w.X, w.Xref[samp], Npm, Np_s)
+    assert np.array_equal(idx.cpu().numpy()[samp], ref_idx)
+    ref = O.alc_select(w.X, w.Xref[samp], ref_idx, w.n0, n_s, w.d, w.g, Np=Np_s, nmax=nmax, topk=4)
+    sel = s["sel"].cpu().numpy()[samp]
+    div = compare_selection(sel, ref, n_s, w.n0, w.g)
+    assert len(div) <= 2
+    d_gpu = m["d"].cpu().numpy()[samp]
+    ref_m = O.mle(w.X, w.Y, sel, n_s, w.d, w.g, *w.mle)
+    np.testing.assert_allclose(d_gpu, ref_m["d"], rtol=1e-6)
+    ref_p = O.predict(w.X, w.Y, w.Xref[samp], sel, n_s, d_gpu, w.g)
+    check_pred(pr["mean"].cpu().numpy()[samp], pr["s2"].cpu().numpy()[samp], ref_p, w.X, w.Y,
+               w.Xref[samp], sel, n_s, d_gpu, w.g)

@@ -257,6 +257,53 @@ def test_mle_finds_grid_maximum(orc):
             assert r["d2llik"][m] < 0
 
 
+def test_two_stage_full_gp_special_case(orc):
+    # n = N' = N: the design of every round is the whole design whatever d, so
+    # the second round of Fig. 1 steps 2-3 (step 4) leaves d at the first
+    # round's estimate, and the prediction is the full GP (Eqs. predgp,
+    # preds2, direct inverse) at the maximiser of its likelihood, here found
+    # by a grid on the closed form of Eq. (gpk) with a direct log-determinant
+    rng = np.random.default_rng(31)
+    X = rng.uniform(-2, 2, (40, 2))
+    Y = W.toy2d_f(X) + rng.normal(0, 1e-3, 40)
+    Xr = rng.uniform(-2, 2, (3, 2))
+    g = 1e-4
+    r = orc.run_pipeline(X, Y, Xr, 6, 40, 40, 0.5, g, mle_args=(1e-3, 20.0, 30), rounds=2)
+    assert len(r["rounds"]) == 2
+    np.testing.assert_allclose(r["rounds"][1]["d_in"], r["rounds"][0]["d"])
+    np.testing.assert_allclose(r["rounds"][1]["d"], r["rounds"][0]["d"], rtol=1e-8)
+
+    def ll(d):  # Eq. (gpk) up to its constant: -1/2 log|K| - n/2 log(Y^T K^-1 Y)
+        K = kmat(X, X, d) + g * np.eye(40)
+        return -0.5 * np.linalg.slogdet(K)[1] - 20.0 * np.log(Y @ np.linalg.solve(K, Y))
+
+    grid = np.geomspace(0.05, 10.0, 2000)
+    vals = np.array([ll(d) for d in grid])
+    i = int(np.argmax(vals))
+    assert 0 < i < len(grid) - 1
+    for m in range(3):
+        assert grid[i - 1] <= r["d"][m] <= grid[i + 1]
+        mu, s2 = full_gp(X, Y, Xr[m], r["d"][m], g)
+        np.testing.assert_allclose(r["mean"][m], mu, rtol=1e-9, atol=1e-11)
+        np.testing.assert_allclose(r["s2"][m], s2, rtol=1e-7)
+
+
+def test_two_stage_is_a_second_search_at_the_estimates(orc):
+    # rounds = 2: the second design is the greedy search at the first-round
+    # estimates and the second MLE starts from them
+    w = W.borehole(seed=32, N=3_000, M=4, n=20, Np=150)
+    mle = (1e-3, 20.0, 10)
+    r = orc.run_pipeline(w.X, w.Y, w.Xref, 6, 20, 150, 2.0, w.g, mle_args=mle, rounds=2)
+    idx = orc.knn(w.X, w.Xref, 150)
+    s1 = orc.alc_select(w.X, w.Xref, idx, 6, 20, 2.0, w.g)["sel"]
+    d1 = orc.mle(w.X, w.Y, s1, 20, 2.0, w.g, *mle)["d"]
+    s2 = orc.alc_select(w.X, w.Xref, idx, 6, 20, d1, w.g)["sel"]
+    d2 = orc.mle(w.X, w.Y, s2, 20, d1, w.g, *mle)["d"]
+    assert np.array_equal(r["rounds"][0]["sel"], s1) and np.array_equal(r["sel"], s2)
+    np.testing.assert_array_equal(r["d"], d2)
+    assert not np.array_equal(s1, s2)  # the estimates moved the designs
+
+
 def fd5(f, x, h):
     """five-point central difference, truncation error O(h^4)"""
     return (8 * (f(x + h) - f(x - h)) - (f(x + 2 * h) - f(x - 2 * h))) / (12 * h)
