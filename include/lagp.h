@@ -231,8 +231,10 @@ lagp_status lagp_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_t N,
  *   - (1/2) log|K_n| - (n/2) log(psi/2), on the local design (Fig. 1 step 3),
  * with analytic first and second derivatives in d, all in FP64.  Step rule:
  * Newton step -l'/l'' when l'' < 0, else doubling/halving in the gradient's
- * direction; proposals are clipped to [dmin, dmax] and halved (at most 20
- * times) until l does not decrease; stop when the step is below 1e-10 d,
+ * direction; proposals are clipped to [dmin, dmax]; a Newton step no longer
+ * than 1e-3 d is taken as it is (near the maximiser the rise in l it brings
+ * is below the FP64 resolution of l), any other proposal is halved (at most
+ * 20 times) until l does not decrease; stop when the step is below 1e-10 d,
  * when no halving recovers an increase, or after max_iter iterations.
  *   d       M lengthscales, in: starting values, out: estimates
  *   llik, dllik, d2llik   M FP64 outputs at the final d (any may be NULL)

@@ -602,11 +602,16 @@ static int mle_one(const double *X, const double *Y, int p, const int32_t *s, in
         double dn = 0.0;
         orc_lik nxt = cur;
         int accepted = 0;
+        /* a short Newton step near the maximiser raises l by about
+         * l'^2 / (2 |l''|), below the FP64 resolution of l there, so it is
+         * taken without comparing l values; every other step must not lower
+         * l, halving it at most 20 times */
+        const int short_newton = cur.d2l < 0.0 && fabs(delta) <= 1e-3 * *d;
         for (int h = 0; h <= 20; h++) {
             dn = *d + delta;
             if (dn < dmin) dn = dmin;
             if (dn > dmax) dn = dmax;
-            if (llik_one(X, Y, p, s, nm, dn, g, &nxt) == ORC_OK && nxt.l >= cur.l) {
+            if (llik_one(X, Y, p, s, nm, dn, g, &nxt) == ORC_OK && (short_newton || nxt.l >= cur.l)) {
                 accepted = 1;
                 break;
             }
@@ -663,6 +668,28 @@ int orc_mle(const double *X, const double *Y, int64_t N, int p, int64_t M,
  *   s2 = psi v / n,   ds2 = (dpsi v + psi dv) / n.
  * For t = d: Kt = K' (as in the likelihood), kx_t = (Dx/d^2) o kx;
  * for t = g: Kt = I, kx_t = 0. */
+/* Triangular solves with the row-major lower Cholesky factor L (n x n):
+ * x = L^{-1} r (forward) and x = L^{-T} r (backward). */
+static void fwd_sub(const double *L, int n, const double *r, double *x) {
+    for (int i = 0; i < n; i++) {
+        double t = r[i];
+        for (int k = 0; k < i; k++) t -= L[i * n + k] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+}
+
+static void bwd_sub(const double *L, int n, const double *r, double *x) {
+    for (int i = n - 1; i >= 0; i--) {
+        double t = r[i];
+        for (int k = i + 1; k < n; k++) t -= L[k * n + i] * x[k];
+        x[i] = t / L[i * n + i];
+    }
+}
+
+/* a = K^{-1} y and b = K^{-1} kx are applied through the Cholesky factor
+ * K = L L^T, and kx^T K^{-1} kx as |L^{-1} kx|^2: the explicit inverse and
+ * the difference (1 + g) - kx^T b lose about eps cond(K) / v relative in v
+ * (v ~ g near the design), which the g-derivative of s2 amplifies. */
 static int pgrad_one(const double *X, const double *Y, int p, const double *x, const int32_t *s,
                      int nm, double d, double g, double out[5]) {
     size_t nn = (size_t)nm * nm;
@@ -687,23 +714,19 @@ static int pgrad_one(const double *X, const double *Y, int p, const double *x, c
             K1[i * nm + k] = (dd / (d * d)) * e;
         }
     }
-    if (spd_inverse(K, nm, Ki) != 0) {
+    double *L = (double *)malloc(sizeof(double) * nn);
+    double *w = (double *)malloc(sizeof(double) * (size_t)nm); /* L^{-1} kx, then L^{-1} y */
+    if (cholesky(K, nm, L) != 0 || spd_inverse(K, nm, Ki) != 0) {
         rc = ORC_ENOTPD;
     } else {
-        for (int i = 0; i < nm; i++) {
-            double ta = 0.0, tb = 0.0;
-            for (int k = 0; k < nm; k++) {
-                ta += Ki[i * nm + k] * y[k];
-                tb += Ki[i * nm + k] * kx[k];
-            }
-            a[i] = ta;
-            b[i] = tb;
-        }
-        double psi = 0.0, kk = 0.0;
-        for (int i = 0; i < nm; i++) {
-            psi += y[i] * a[i];
-            kk += kx[i] * b[i];
-        }
+        fwd_sub(L, nm, kx, w);
+        double kk = 0.0;
+        for (int i = 0; i < nm; i++) kk += w[i] * w[i];
+        bwd_sub(L, nm, w, b);
+        fwd_sub(L, nm, y, w);
+        bwd_sub(L, nm, w, a);
+        double psi = 0.0;
+        for (int i = 0; i < nm; i++) psi += y[i] * a[i];
         double v = (1.0 + g) - kk;
         /* t = d */
         double kxd_a = 0.0, bK1a = 0.0, aK1a = 0.0, kxd_b = 0.0, bK1b = 0.0;
@@ -744,6 +767,8 @@ static int pgrad_one(const double *X, const double *Y, int p, const double *x, c
     free(y);
     free(a);
     free(b);
+    free(L);
+    free(w);
     return rc;
 }
 

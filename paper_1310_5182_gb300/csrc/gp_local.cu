@@ -40,8 +40,10 @@ __device__ double block_sum(double v, double *red, const Blk &b) {
 }
 
 // Lower Cholesky of the symmetric n x n matrix A (lower triangle used) into L,
-// left-looking.  Returns false (block-uniform) if a pivot is not positive.
-__device__ bool block_cholesky(const double *A, double *L, int n, int ld, int *flag, const Blk &b) {
+// left-looking, with rd = 1 / diag(L).  Returns false (block-uniform) if a
+// pivot is not positive.
+__device__ bool block_cholesky(const double *A, double *L, double *rd, int n, int ld, int *flag,
+                               const Blk &b) {
     if (b.tid == 0) *flag = 1;
     for (int c = 0; c < n; c++) {
         if (b.warp == 0) {
@@ -55,35 +57,43 @@ __device__ bool block_cholesky(const double *A, double *L, int n, int ld, int *f
             }
         }
         __syncthreads();
-        const double lcc = L[(size_t)c * ld + c];
+        const double rcc = 1.0 / L[(size_t)c * ld + c];
+        if (b.tid == 0) rd[c] = rcc;
         for (int i = c + 1 + b.tid; i < n; i += GP_THREADS) {
-            double s = A[(size_t)i * ld + c];
-            for (int k = 0; k < c; k++) s = fma(-L[(size_t)i * ld + k], L[(size_t)c * ld + k], s);
-            L[(size_t)i * ld + c] = s / lcc;
+            double s0 = A[(size_t)i * ld + c], s1 = 0.0;
+            int k = 0;
+            for (; k + 2 <= c; k += 2) {  // two chains: half the dependent FMA latency
+                s0 = fma(-L[(size_t)i * ld + k], L[(size_t)c * ld + k], s0);
+                s1 = fma(-L[(size_t)i * ld + k + 1], L[(size_t)c * ld + k + 1], s1);
+            }
+            if (k < c) s0 = fma(-L[(size_t)i * ld + k], L[(size_t)c * ld + k], s0);
+            L[(size_t)i * ld + c] = (s0 + s1) * rcc;
         }
         __syncthreads();
     }
     return *flag != 0;
 }
 
-// x = L^{-1} rhs by forward substitution, one warp.
-__device__ void warp_forward(const double *L, int ld, const double *rhs, double *x, int n, int lane) {
+// x = L^{-1} rhs by forward substitution, one warp; rd = 1 / diag(L).
+__device__ void warp_forward(const double *L, int ld, const double *rd, const double *rhs, double *x,
+                             int n, int lane) {
     for (int i = 0; i < n; i++) {
         double s = 0.0;
         for (int k = lane; k < i; k += 32) s = fma(L[(size_t)i * ld + k], x[k], s);
         s = warp_sum(s);
-        if (lane == 0) x[i] = (rhs[i] - s) / L[(size_t)i * ld + i];
+        if (lane == 0) x[i] = (rhs[i] - s) * rd[i];
         __syncwarp();
     }
 }
 
-// x = L^{-T} rhs by backward substitution, one warp.
-__device__ void warp_backward(const double *L, int ld, const double *rhs, double *x, int n, int lane) {
+// x = L^{-T} rhs by backward substitution, one warp; rd = 1 / diag(L).
+__device__ void warp_backward(const double *L, int ld, const double *rd, const double *rhs, double *x,
+                              int n, int lane) {
     for (int i = n - 1; i >= 0; i--) {
         double s = 0.0;
         for (int k = i + 1 + lane; k < n; k += 32) s = fma(L[(size_t)k * ld + i], x[k], s);
         s = warp_sum(s);
-        if (lane == 0) x[i] = (rhs[i] - s) / L[(size_t)i * ld + i];
+        if (lane == 0) x[i] = (rhs[i] - s) * rd[i];
         __syncwarp();
     }
 }
@@ -143,10 +153,11 @@ __device__ void build_D(const double *xd, int nm, int p, double *D, int ld, cons
 
 // K = exp(-D/d) + g I (full symmetric).
 __device__ void build_K(const double *D, int nm, int ld, double d, double g, double *K, const Blk &b) {
+    const double ninv_d = -1.0 / d;
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
         int i = e / nm, k = e - i * nm;
         if (k <= i) {
-            double v = exp(-D[(size_t)i * ld + k] / d);
+            double v = exp(D[(size_t)i * ld + k] * ninv_d);
             K[(size_t)i * ld + k] = v + (i == k ? g : 0.0);
             K[(size_t)k * ld + i] = v + (i == k ? g : 0.0);
         }
@@ -157,11 +168,12 @@ __device__ void build_K(const double *D, int nm, int ld, double d, double g, dou
 // log-likelihood of Eq. (gpk) at d: needs K built; leaves L and a = K^{-1} y.
 // Returns false if K is not positive definite.
 __device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, double *a, double *tmp,
-                           double *red, int *flag, double *out_l, double *out_psi, const Blk &b) {
-    if (!block_cholesky(W.K, W.L, nm, ld, flag, b)) return false;
+                           double *rd, double *red, int *flag, double *out_l, double *out_psi,
+                           const Blk &b) {
+    if (!block_cholesky(W.K, W.L, rd, nm, ld, flag, b)) return false;
     if (b.warp == 0) {
-        warp_forward(W.L, ld, y, tmp, nm, b.lane);
-        warp_backward(W.L, ld, tmp, a, nm, b.lane);
+        warp_forward(W.L, ld, rd, y, tmp, nm, b.lane);
+        warp_backward(W.L, ld, rd, tmp, a, nm, b.lane);
     }
     __syncthreads();
     double ld_part = 0.0, psi_part = 0.0;
@@ -177,8 +189,11 @@ __device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, dou
     return true;
 }
 
-// K^{-1} from L (needs L): Li = L^{-1}, Ki = Li^T Li.
-__device__ void inverse_from_L(const GpWork &W, int nm, int ld, const Blk &b) {
+// K^{-1} from L (needs L): Li = L^{-1}, Ki = Li^T Li.  rdiag: nm doubles of
+// scratch for the reciprocals of L's diagonal.
+__device__ void inverse_from_L(const GpWork &W, int nm, int ld, double *rdiag, const Blk &b) {
+    for (int i = b.tid; i < nm; i += GP_THREADS) rdiag[i] = 1.0 / W.L[(size_t)i * ld + i];
+    __syncthreads();
     for (int c = b.warp; c < nm; c += GP_WARPS) {  // column c of L^{-1}
         for (int i = 0; i < nm; i++) {
             double val;
@@ -188,7 +203,7 @@ __device__ void inverse_from_L(const GpWork &W, int nm, int ld, const Blk &b) {
                 double s = 0.0;
                 for (int k = c + b.lane; k < i; k += 32) s = fma(W.L[(size_t)i * ld + k], W.Li[(size_t)k * ld + c], s);
                 s = warp_sum(s);
-                val = ((i == c ? 1.0 : 0.0) - s) / W.L[(size_t)i * ld + i];
+                val = ((i == c ? 1.0 : 0.0) - s) * rdiag[i];
             }
             if (b.lane == 0) W.Li[(size_t)i * ld + c] = val;
             __syncwarp();
@@ -212,29 +227,35 @@ struct Derivs {
 };
 
 // First and second d-derivatives of l (and dl/dg); needs K, L, a, psi.
+// K' = (D/d^2) o E goes into Li's storage once L^{-1} is no longer needed.
 __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const double *a, double psi,
                               double *t1, double *t2, double *red, const Blk &b) {
-    inverse_from_L(W, nm, ld, b);
-    const double d2 = d * d, d3 = d2 * d, d4 = d2 * d2;
-    // K' into D's upper use: compute on the fly K'_ik = (D/d^2) E, E = K - g I
-    // A1 = K^{-1} K'
+    inverse_from_L(W, nm, ld, t2, b);
+    const double id2 = 1.0 / (d * d), id3 = id2 / d, id4 = id2 * id2;
+    double *Kp = W.Li;
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
-        int i = e / nm, k = e - i * nm;
-        double s = 0.0;
-        for (int r = 0; r < nm; r++) {
-            double Dr = W.D[(size_t)r * ld + k];
-            double Er = (r == k) ? 0.0 : W.K[(size_t)r * ld + k];
-            s = fma(W.Ki[(size_t)i * ld + r], (Dr / d2) * Er, s);
+        const int i = e / nm, k = e - i * nm;
+        const double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
+        Kp[(size_t)i * ld + k] = (W.D[(size_t)i * ld + k] * id2) * E;
+    }
+    __syncthreads();
+    // A1 = K^{-1} K' (two accumulation chains per element)
+    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+        const int i = e / nm, k = e - i * nm;
+        const double *Kir = W.Ki + (size_t)i * ld;
+        double s0 = 0.0, s1 = 0.0;
+        int r = 0;
+        for (; r + 2 <= nm; r += 2) {
+            s0 = fma(Kir[r], Kp[(size_t)r * ld + k], s0);
+            s1 = fma(Kir[r + 1], Kp[(size_t)(r + 1) * ld + k], s1);
         }
-        W.A1[(size_t)i * ld + k] = s;
+        if (r < nm) s0 = fma(Kir[r], Kp[(size_t)r * ld + k], s0);
+        W.A1[(size_t)i * ld + k] = s0 + s1;
     }
     // t1 = K' a
     for (int i = b.tid; i < nm; i += GP_THREADS) {
         double s = 0.0;
-        for (int k = 0; k < nm; k++) {
-            double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
-            s = fma((W.D[(size_t)i * ld + k] / d2) * E, a[k], s);
-        }
+        for (int k = 0; k < nm; k++) s = fma(Kp[(size_t)i * ld + k], a[k], s);
         t1[i] = s;
     }
     __syncthreads();
@@ -244,7 +265,7 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
         trA1A1 = fma(W.A1[(size_t)i * ld + k], W.A1[(size_t)k * ld + i], trA1A1);
         double Dik = W.D[(size_t)i * ld + k];
         double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
-        double K2 = (Dik * Dik / d4 - 2.0 * Dik / d3) * E;
+        double K2 = (Dik * Dik * id4 - 2.0 * Dik * id3) * E;
         trKiK2 = fma(W.Ki[(size_t)i * ld + k], K2, trKiK2);
         aK2a = fma(a[i] * K2, a[k], aK2a);
         if (i == k) {
@@ -283,7 +304,7 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
 }
 
 struct GpShared {
-    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *xq;
+    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *rd, *xq;
 };
 
 __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
@@ -297,7 +318,8 @@ __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
     S.t3 = S.t2 + nmax;
     S.kx = S.t3 + nmax;
     S.dx = S.kx + nmax;
-    S.xq = S.dx + nmax;
+    S.rd = S.dx + nmax;  // 1 / diag of the current Cholesky factor
+    S.xq = S.rd + nmax;
     return S;
 }
 
@@ -335,11 +357,11 @@ predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws
             build_K(W.D, nm, ld, d, g, W.K, b);
             for (int t = b.tid; t < nm; t += GP_THREADS) S.kx[t] = exp(-sqd(S.xq, S.xd + (size_t)t * p, p) / d);
             __syncthreads();
-            if (!block_cholesky(W.K, W.L, nm, ld, &s_chol, b)) {
+            if (!block_cholesky(W.K, W.L, S.rd, nm, ld, &s_chol, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                if (b.warp == 0) warp_forward(W.L, ld, S.y, S.t1, nm, b.lane);   // z
-                if (b.warp == 1) warp_forward(W.L, ld, S.kx, S.t2, nm, b.lane);  // w
+                if (b.warp == 0) warp_forward(W.L, ld, S.rd, S.y, S.t1, nm, b.lane);   // z
+                if (b.warp == 1) warp_forward(W.L, ld, S.rd, S.kx, S.t2, nm, b.lane);  // w
                 __syncthreads();
                 double m_p = 0.0, psi_p = 0.0, kk_p = 0.0;
                 for (int i = b.tid; i < nm; i += GP_THREADS) {
@@ -398,7 +420,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
             d = fmin(fmax(d, dmin), dmax);
             build_D(S.xd, nm, p, W.D, ld, b);
             build_K(W.D, nm, ld, d, g, W.K, b);
-            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &l, &psi, b)) {
+            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
                 dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
@@ -409,10 +431,14 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     else delta = (dr.dl > 0.0) ? d : -0.5 * d;
                     bool accepted = false;
                     double dn = d, ln = l, psin = psi;
+                    // a short Newton step near the maximiser raises l below the
+                    // FP64 resolution of l: taken without comparing l values
+                    const bool short_newton = dr.d2l < 0.0 && fabs(delta) <= 1e-3 * d;
                     for (int h = 0; h <= 20; h++) {
                         dn = fmin(fmax(d + delta, dmin), dmax);
                         build_K(W.D, nm, ld, dn, g, W.K, b);
-                        if (llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &ln, &psin, b) && ln >= l) {
+                        if (llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &ln, &psin, b) &&
+                            (short_newton || ln >= l)) {
                             accepted = true;
                             break;
                         }
@@ -421,7 +447,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     if (!accepted) {
                         // restore K, L, a at the current d
                         build_K(W.D, nm, ld, d, g, W.K, b);
-                        llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &l, &psi, b);
+                        llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b);
                         break;
                     }
                     const double step = fabs(dn - d);
@@ -476,27 +502,32 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
             build_D(S.xd, nm, p, W.D, ld, b);
             build_K(W.D, nm, ld, d, g, W.K, b);
             double l, psi;
-            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, red, &s_chol, &l, &psi, b)) {
+            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
                 Derivs dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
-                // kx, kx_d = (Dx/d^2) kx ; b = K^{-1} kx (t1), K'a (t2), K'b (t3)
+                // kx, kx_d = (Dx/d^2) kx ; b = K^{-1} kx (t1) by the two triangular
+                // solves (w = L^{-1} kx in t3, v = 1 + g - w^T w: no explicit
+                // inverse, no cancellation against k^T b), K'a (t2), K'b (t3)
+                const double id2 = 1.0 / d2;
                 for (int t = b.tid; t < nm; t += GP_THREADS) {
                     S.dx[t] = sqd(S.xq, S.xd + (size_t)t * p, p);
                     S.kx[t] = exp(-S.dx[t] / d);
                 }
                 __syncthreads();
-                for (int i = b.tid; i < nm; i += GP_THREADS) {
-                    double s = 0.0;
-                    for (int k = 0; k < nm; k++) s = fma(W.Ki[(size_t)i * ld + k], S.kx[k], s);
-                    S.t1[i] = s;
+                if (b.warp == 0) {
+                    warp_forward(W.L, ld, S.rd, S.kx, S.t3, nm, b.lane);
+                    warp_backward(W.L, ld, S.rd, S.t3, S.t1, nm, b.lane);
                 }
                 __syncthreads();
+                double ww_p = 0.0;
+                for (int i = b.tid; i < nm; i += GP_THREADS) ww_p = fma(S.t3[i], S.t3[i], ww_p);
+                const double ww = block_sum(ww_p, red, b);
                 for (int i = b.tid; i < nm; i += GP_THREADS) {
                     double sa = 0.0, sb = 0.0;
                     for (int k = 0; k < nm; k++) {
                         double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
-                        double K1 = (W.D[(size_t)i * ld + k] / d2) * E;
+                        double K1 = (W.D[(size_t)i * ld + k] * id2) * E;
                         sa = fma(K1, S.a[k], sa);
                         sb = fma(K1, S.t1[k], sb);
                     }
@@ -504,10 +535,10 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
                     S.t3[i] = sb;
                 }
                 __syncthreads();
-                double kxd_a = 0, bK1a = 0, aK1a = 0, kxd_b = 0, bK1b = 0, ba = 0, aa = 0, bb = 0, kk = 0;
+                double kxd_a = 0, bK1a = 0, aK1a = 0, kxd_b = 0, bK1b = 0, ba = 0, aa = 0, bb = 0;
                 for (int i = b.tid; i < nm; i += GP_THREADS) {
                     const double kxi = S.kx[i];
-                    const double kxdi = (S.dx[i] / d2) * kxi;
+                    const double kxdi = (S.dx[i] * id2) * kxi;
                     kxd_a = fma(kxdi, S.a[i], kxd_a);
                     kxd_b = fma(kxdi, S.t1[i], kxd_b);
                     bK1a = fma(S.t1[i], S.t2[i], bK1a);
@@ -516,7 +547,6 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
                     ba = fma(S.t1[i], S.a[i], ba);
                     aa = fma(S.a[i], S.a[i], aa);
                     bb = fma(S.t1[i], S.t1[i], bb);
-                    kk = fma(kxi, S.t1[i], kk);
                 }
                 kxd_a = block_sum(kxd_a, red, b);
                 kxd_b = block_sum(kxd_b, red, b);
@@ -526,8 +556,7 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
                 ba = block_sum(ba, red, b);
                 aa = block_sum(aa, red, b);
                 bb = block_sum(bb, red, b);
-                kk = block_sum(kk, red, b);
-                const double v = (1.0 + g) - kk;
+                const double v = (1.0 + g) - ww;  // = 1 + g - k^T K^{-1} k
                 r[0] = kxd_a - bK1a;
                 r[1] = -ba;
                 r[2] = (-aK1a * v + psi * (-2.0 * kxd_b + bK1b)) / nm;
@@ -562,7 +591,9 @@ lagp_status prepare(lagp_ctx *ctx, const GpArgs &a, Kern kern, GpLaunch &L) {
     L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p) * 8 + 64;
     if (L.smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "n_max x p too large");
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-    int per_sm = 2;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, GP_THREADS, L.smem);
+    const int per_sm = occ > 0 ? occ : 1;  // latency-bound FP64 phases: as many CTAs as fit
     int64_t grid = (int64_t)ctx->num_sms * per_sm;
     if (grid > a.M) grid = a.M;
     if (grid < 1) grid = 1;

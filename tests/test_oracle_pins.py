@@ -337,6 +337,50 @@ def _paper_table():
     return {int(r[0]): (int(r[1]), int(r[2]), float(r[4])) for r in rows}
 
 
+def test_predict_grad_g_accuracy_against_50_digit_evaluation(orc):
+    # d s2 / d g = (-a^T a v + psi (1 + b^T b)) / n (Eq. preds2 with
+    # d(K^{-1})/dg = -K^{-1} K^{-1}; a = K^{-1} y, b = K^{-1} k, v = 1 + g -
+    # k^T b) at locations where v ~ g and cond(K) ~ 2.6e5: the oracle's FP64
+    # value must agree with the same formulas evaluated in 50-digit decimal
+    # arithmetic (own Cholesky) on the same kernel values
+    from decimal import Decimal, getcontext
+    getcontext().prec = 50
+    w = W.toy2d(seed=14, N=3_000, M=20, Np=200, n=30)
+    idx = orc.knn(w.X, w.Xref, 200)
+    sel = orc.alc_select(w.X, w.Xref, idx, 6, 30, w.d, w.g)["sel"]
+    r = orc.predict_grad(w.X, w.Y, w.Xref, sel, 30, w.d, w.g)
+    n = 30
+    for m in (0, 2, 16):
+        rows = sel[m, :n]
+        A = w.X[rows]
+        K = kmat(A, A, w.d) + w.g * np.eye(n)
+        k = kmat(A, w.Xref[m][None], w.d)[:, 0]
+        Kd = [[Decimal(float(K[i, j])) for j in range(n)] for i in range(n)]
+        L = [[Decimal(0)] * n for _ in range(n)]
+        for j in range(n):
+            s = Kd[j][j] - sum(L[j][q] * L[j][q] for q in range(j))
+            L[j][j] = s.sqrt()
+            for i in range(j + 1, n):
+                L[i][j] = (Kd[i][j] - sum(L[i][q] * L[j][q] for q in range(j))) / L[j][j]
+
+        def solve(rhs):
+            z = [Decimal(0)] * n
+            for i in range(n):
+                z[i] = (rhs[i] - sum(L[i][q] * z[q] for q in range(i))) / L[i][i]
+            x = [Decimal(0)] * n
+            for i in reversed(range(n)):
+                x[i] = (z[i] - sum(L[q][i] * x[q] for q in range(i + 1, n))) / L[i][i]
+            return x
+
+        yv = [Decimal(float(v)) for v in w.Y[rows]]
+        kv = [Decimal(float(v)) for v in k]
+        a, b = solve(yv), solve(kv)
+        psi = sum(p * q for p, q in zip(yv, a))
+        v = 1 + Decimal(w.g) - sum(p * q for p, q in zip(kv, b))
+        exact = (-sum(q * q for q in a) * v + psi * (1 + sum(q * q for q in b))) / n
+        assert abs(r["ds2_dg"][m] - float(exact)) <= 1e-8 * abs(float(exact)), m
+
+
 def test_borehole_mse_order_of_paper_table(orc):
     """Loose pin: with d = 2.0 on unit-cube inputs, the out-of-sample MSE of the
     unstandardised borehole response is within a small factor of the paper's
