@@ -53,6 +53,10 @@ def parse():
                          "uneven borehole with MLE)")
     ap.add_argument("--extra", action="store_true",
                     help="also time the 3-d slab grid and the 4M-point borehole (both with MLE)")
+    ap.add_argument("--config", default=None, choices=sorted(W.CONFIGS),
+                    help="time only this configuration's leg and print it as one JSON line "
+                         "(per-configuration timing and profiler captures; not the headline)")
+    ap.add_argument("--N", type=int, default=None, help="design size override for --config")
     ap.add_argument("--M", type=int, default=None,
                     help="reference locations per GPU (default: the workload's 10,000; smaller "
                          "values are for profiler captures, not bench lines)")
@@ -106,7 +110,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": None, "dram_bytes_per_location": None}
+ALC_TRAFFIC = {"sha256": "b79fb987936114fb4c332b7bd29aeedfdb7a51708a7eee0a6da4bdeee2cec960",
+               "dram_bytes_per_location": (3.961646e9 + 0.669469e9) / 3040}
 
 
 def alc_source_hash():
@@ -280,6 +285,23 @@ def other_configs(L, dev, args, flush):
         out["borehole8d_N4000000_M100000_n50_Nprime2000_mle"] = config_leg(L, dev, w5, "f32bulk", 2, 1,
                                                                            flush)
     return out
+
+
+def run_config(args):
+    """One configuration's leg alone (sizes overridable for small captures)."""
+    import torch
+    import paper_1310_5182_gb300 as L
+    dev = torch.device("cuda", 0)
+    kw = {}
+    if args.N is not None:
+        kw["N"] = args.N
+    if args.M is not None:
+        kw["M"] = args.M
+    w = W.CONFIGS[args.config](**kw)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = config_leg(L, dev, w, args.prec, args.steps, args.warmup, flush)
+    out.update(config=args.config, overrides=kw)
+    print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------- ours
@@ -496,6 +518,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.config:
+        run_config(args)
         return
     if world > 1:
         import torch

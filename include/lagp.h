@@ -290,7 +290,7 @@ lagp_status lagp_predict_noalloc(lagp_ctx *ctx, const void *X, const void *Y, in
  * desired"): each round searches the designs at the current per-location d
  * and then moves d to the MLE on that design, starting from the current d;
  * the prediction (step 5) uses the last design and estimate.  r = 2 is the
- * two-stage scheme of Sec. 3.1 (designs re-searched with the local
+ * two-stage scheme of Sec. 2.2 (designs re-searched with the local
  * estimates).  All array arguments are HOST pointers; the inputs are copied
  * to the device, and the outputs copied back, inside the call, which returns
  * after the outputs are in host memory.

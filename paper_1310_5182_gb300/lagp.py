@@ -137,9 +137,13 @@ def _dev(t: torch.Tensor, name, dtype=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _opt_i32(v, M, device, name):
-    """None -> NULL pointer; int / array -> int32 CUDA tensor of length M."""
+def _opt_i32(v, M, device, name, uniform=None):
+    """None -> NULL pointer; array -> int32 CUDA tensor of length M.  A plain
+    integer equal to `uniform` (the value the C API assumes for NULL) also
+    becomes NULL, so that no device copy is made for it."""
     if v is None:
+        return None, None
+    if uniform is not None and isinstance(v, (int, np.integer)) and int(v) == int(uniform):
         return None, None
     t = torch.as_tensor(v, dtype=torch.int32, device=device)
     if t.dim() == 0:
@@ -151,6 +155,8 @@ def _opt_i32(v, M, device, name):
 
 
 def _per_loc_f64(v, M, device):
+    if isinstance(v, (int, float, np.floating, np.integer)):
+        return torch.full((M,), float(v), dtype=torch.float64, device=device)
     t = torch.as_tensor(v, dtype=torch.float64, device=device)
     if t.dim() == 0:
         t = t.expand(M)
@@ -186,10 +192,12 @@ def lagp_autotune(X, Xref, idx, n0, n, d, g, prec="f32bulk", Y=None, Nprime=None
     ctx = context(X.device)
     N, p = X.shape
     M, Npmax = idx.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
-    if n_max is None:
-        n_max = int(nt.max().item()) if nt is not None and M else int(n)
-    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    if n_max is None and isinstance(n, (int, np.integer)):
+        n_max = int(n)
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
+    if n_max is None:  # per-location n without n_max: one device sync
+        n_max = int(nt.max().item()) if M else 1
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime", uniform=Npmax)
     dt = _per_loc_f64(d, M, X.device)
     best = ctypes.c_int32(0)
     _check(_lib.lagp_autotune(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref", X.dtype), M,
@@ -233,7 +241,7 @@ def lagp_knn(X: torch.Tensor, Xref: torch.Tensor, Nprime_max: int, Nprime=None):
     M = Xref.shape[0]
     if Xref.dtype != X.dtype or Xref.shape[1] != p:
         raise ValueError("Xref must match X in dtype and p")
-    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime", uniform=Nprime_max)
     idx = torch.empty((M, Nprime_max), dtype=torch.int32, device=X.device)
     status = torch.empty(M, dtype=torch.int32, device=X.device)
     if M:
@@ -250,10 +258,12 @@ def lagp_alc_select(X, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, n_ma
     ctx = context(X.device)
     N, p = X.shape
     M, Npmax = idx.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
-    if n_max is None:
-        n_max = int(nt.max().item()) if nt is not None and M else int(n)
-    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    if n_max is None and isinstance(n, (int, np.integer)):
+        n_max = int(n)
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
+    if n_max is None:  # per-location n without n_max: one device sync
+        n_max = int(nt.max().item()) if M else 1
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime", uniform=Npmax)
     dt = _per_loc_f64(d, M, X.device)
     sel = torch.empty((M, n_max), dtype=torch.int32, device=X.device)
     status = torch.empty(M, dtype=torch.int32, device=X.device)
@@ -274,10 +284,12 @@ def lagp_alc_predict(X, Y, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, 
     ctx = context(X.device)
     N, p = X.shape
     M, Npmax = idx.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
-    if n_max is None:
-        n_max = int(nt.max().item()) if nt is not None and M else int(n)
-    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime")
+    if n_max is None and isinstance(n, (int, np.integer)):
+        n_max = int(n)
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
+    if n_max is None:  # per-location n without n_max: one device sync
+        n_max = int(nt.max().item()) if M else 1
+    Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime", uniform=Npmax)
     dt = _per_loc_f64(d, M, X.device)
     sel = torch.empty((M, n_max), dtype=torch.int32, device=X.device)
     status = torch.empty(M, dtype=torch.int32, device=X.device)
@@ -300,7 +312,7 @@ def lagp_predict(X, Y, Xref, sel, n, d, g):
     ctx = context(X.device)
     N, p = X.shape
     M, n_max = sel.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
     dt = _per_loc_f64(d, M, X.device)
     out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in ("mean", "s2", "df")}
     status = torch.empty(M, dtype=torch.int32, device=X.device)
@@ -323,7 +335,7 @@ def lagp_predict_noalloc(X, Y, Xref, sel, n, d, g, out=None):
     ctx = context(X.device)
     N, p = X.shape
     M, n_max = sel.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
     dt = d if (isinstance(d, torch.Tensor) and d.dtype == torch.float64 and d.is_cuda
                and d.numel() == M and d.is_contiguous()) else _per_loc_f64(d, M, X.device)
     if out is None:
@@ -344,7 +356,7 @@ def lagp_mle_step(X, Y, sel, n, d0, g, dmin, dmax, max_iter):
     ctx = context(X.device)
     N, p = X.shape
     M, n_max = sel.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
     d = _per_loc_f64(d0, M, X.device)
     out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in ("llik", "dllik", "d2llik")}
     iters = torch.empty(M, dtype=torch.int32, device=X.device)
@@ -365,7 +377,7 @@ def lagp_predict_grad(X, Y, Xref, sel, n, d, g):
     ctx = context(X.device)
     N, p = X.shape
     M, n_max = sel.shape
-    nt, npp = _opt_i32(n, M, X.device, "n")
+    nt, npp = _opt_i32(n, M, X.device, "n", uniform=n_max)
     dt = _per_loc_f64(d, M, X.device)
     keys = ("dmean_dd", "dmean_dg", "ds2_dd", "ds2_dg", "dllik_dd", "dllik_dg")
     out = {k: torch.empty(M, dtype=torch.float64, device=X.device) for k in keys}
