@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "device_util.cuh"
+#include "exp64.cuh"
 #include "lagp_internal.h"
 
 namespace {
@@ -138,6 +139,15 @@ __device__ double sqd(const double *u, const double *v, int p) {
     return s;
 }
 
+// Row i and column k <= i of the e-th element of a lower triangle stored by rows.
+__device__ __forceinline__ void tri_index(int e, int &i, int &k) {
+    int r = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= e) r++;
+    while (r * (r + 1) / 2 > e) r--;
+    i = r;
+    k = e - r * (r + 1) / 2;
+}
+
 // D (squared distances, lower triangle and diagonal) of the design.
 __device__ void build_D(const double *xd, int nm, int p, double *D, int ld, const Blk &b) {
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
@@ -151,16 +161,17 @@ __device__ void build_D(const double *xd, int nm, int p, double *D, int ld, cons
     __syncthreads();
 }
 
-// K = exp(-D/d) + g I (full symmetric).
-__device__ void build_K(const double *D, int nm, int ld, double d, double g, double *K, const Blk &b) {
+// K = exp(-D/d) + g I (full symmetric), over the lower triangle, with the
+// table-driven exponential (etab: its table in shared memory).
+__device__ void build_K(const double *D, int nm, int ld, double d, double g, double *K,
+                        const double *etab, const Blk &b) {
     const double ninv_d = -1.0 / d;
-    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
-        int i = e / nm, k = e - i * nm;
-        if (k <= i) {
-            double v = exp(D[(size_t)i * ld + k] * ninv_d);
-            K[(size_t)i * ld + k] = v + (i == k ? g : 0.0);
-            K[(size_t)k * ld + i] = v + (i == k ? g : 0.0);
-        }
+    for (int e = b.tid; e < nm * (nm + 1) / 2; e += GP_THREADS) {
+        int i, k;
+        tri_index(e, i, k);
+        const double v = exp64_tang(D[(size_t)i * ld + k] * ninv_d, etab) + (i == k ? g : 0.0);
+        K[(size_t)i * ld + k] = v;
+        K[(size_t)k * ld + i] = v;
     }
     __syncthreads();
 }
@@ -189,35 +200,36 @@ __device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, dou
     return true;
 }
 
-// K^{-1} from L (needs L): Li = L^{-1}, Ki = Li^T Li.  rdiag: nm doubles of
-// scratch for the reciprocals of L's diagonal.
-__device__ void inverse_from_L(const GpWork &W, int nm, int ld, double *rdiag, const Blk &b) {
-    for (int i = b.tid; i < nm; i += GP_THREADS) rdiag[i] = 1.0 / W.L[(size_t)i * ld + i];
-    __syncthreads();
-    for (int c = b.warp; c < nm; c += GP_WARPS) {  // column c of L^{-1}
-        for (int i = 0; i < nm; i++) {
-            double val;
-            if (i < c) {
-                val = 0.0;
-            } else {
-                double s = 0.0;
-                for (int k = c + b.lane; k < i; k += 32) s = fma(W.L[(size_t)i * ld + k], W.Li[(size_t)k * ld + c], s);
-                s = warp_sum(s);
-                val = ((i == c ? 1.0 : 0.0) - s) * rdiag[i];
+// K^{-1} from L (needs L and rd = 1 / diag(L)): Li = L^{-1} row by row, the
+// columns of a row in parallel (full-lane FMAs, no reductions), then
+// Ki = Li^T Li.
+__device__ void inverse_from_L(const GpWork &W, int nm, int ld, const double *rd, const Blk &b) {
+    for (int i = 0; i < nm; i++) {
+        const double *Lr = W.L + (size_t)i * ld;
+        for (int c = b.tid; c <= i; c += GP_THREADS) {
+            double s0 = (c == i) ? 1.0 : 0.0, s1 = 0.0;
+            int k = c;
+            for (; k + 2 <= i; k += 2) {  // Li[i][c] = (delta_ic - sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
+                s0 = fma(-Lr[k], W.Li[(size_t)k * ld + c], s0);
+                s1 = fma(-Lr[k + 1], W.Li[(size_t)(k + 1) * ld + c], s1);
             }
-            if (b.lane == 0) W.Li[(size_t)i * ld + c] = val;
-            __syncwarp();
+            if (k < i) s0 = fma(-Lr[k], W.Li[(size_t)k * ld + c], s0);
+            W.Li[(size_t)i * ld + c] = (s0 + s1) * rd[i];
         }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
-        int i = e / nm, k = e - i * nm;
-        if (k <= i) {
-            double s = 0.0;
-            for (int r = i; r < nm; r++) s = fma(W.Li[(size_t)r * ld + i], W.Li[(size_t)r * ld + k], s);
-            W.Ki[(size_t)i * ld + k] = s;
-            W.Ki[(size_t)k * ld + i] = s;
+    for (int e = b.tid; e < nm * (nm + 1) / 2; e += GP_THREADS) {  // lower triangle, mirrored
+        int i, k;
+        tri_index(e, i, k);
+        double s0 = 0.0, s1 = 0.0;
+        int r = i;
+        for (; r + 2 <= nm; r += 2) {
+            s0 = fma(W.Li[(size_t)r * ld + i], W.Li[(size_t)r * ld + k], s0);
+            s1 = fma(W.Li[(size_t)(r + 1) * ld + i], W.Li[(size_t)(r + 1) * ld + k], s1);
         }
+        if (r < nm) s0 = fma(W.Li[(size_t)r * ld + i], W.Li[(size_t)r * ld + k], s0);
+        W.Ki[(size_t)i * ld + k] = s0 + s1;
+        W.Ki[(size_t)k * ld + i] = s0 + s1;
     }
     __syncthreads();
 }
@@ -229,8 +241,8 @@ struct Derivs {
 // First and second d-derivatives of l (and dl/dg); needs K, L, a, psi.
 // K' = (D/d^2) o E goes into Li's storage once L^{-1} is no longer needed.
 __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const double *a, double psi,
-                              double *t1, double *t2, double *red, const Blk &b) {
-    inverse_from_L(W, nm, ld, t2, b);
+                              const double *rd, double *t1, double *t2, double *red, const Blk &b) {
+    inverse_from_L(W, nm, ld, rd, b);
     const double id2 = 1.0 / (d * d), id3 = id2 / d, id4 = id2 * id2;
     double *Kp = W.Li;
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
@@ -304,7 +316,7 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
 }
 
 struct GpShared {
-    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *rd, *xq;
+    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *rd, *xq, *etab;
 };
 
 __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
@@ -320,6 +332,7 @@ __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
     S.dx = S.kx + nmax;
     S.rd = S.dx + nmax;  // 1 / diag of the current Cholesky factor
     S.xq = S.rd + nmax;
+    S.etab = S.xq + p;  // 64: table of exp64_tang
     return S;
 }
 
@@ -337,6 +350,7 @@ predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
+    for (int i = threadIdx.x; i < 64; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     __shared__ double red[GP_WARPS];
@@ -354,7 +368,7 @@ predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws
             const double d = dv[loc], g = a.g;
             for (int i = b.tid; i < p; i += GP_THREADS) S.xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
             build_D(S.xd, nm, p, W.D, ld, b);
-            build_K(W.D, nm, ld, d, g, W.K, b);
+            build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
             for (int t = b.tid; t < nm; t += GP_THREADS) S.kx[t] = exp(-sqd(S.xq, S.xd + (size_t)t * p, p) / d);
             __syncthreads();
             if (!block_cholesky(W.K, W.L, S.rd, nm, ld, &s_chol, b)) {
@@ -393,12 +407,13 @@ struct MleOut {
     int32_t *iters, *status;
 };
 
-__global__ void __launch_bounds__(GP_THREADS)
+__global__ void __launch_bounds__(GP_THREADS, 3)
 mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *counter, double *ws,
            MleOut o) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
+    for (int i = threadIdx.x; i < 64; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     __shared__ double red[GP_WARPS];
@@ -419,11 +434,11 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
             const double g = a.g;
             d = fmin(fmax(d, dmin), dmax);
             build_D(S.xd, nm, p, W.D, ld, b);
-            build_K(W.D, nm, ld, d, g, W.K, b);
+            build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
             if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
+                dr = llik_derivs(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
                 while (it < max_iter) {
                     it++;
                     double delta;
@@ -436,7 +451,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     const bool short_newton = dr.d2l < 0.0 && fabs(delta) <= 1e-3 * d;
                     for (int h = 0; h <= 20; h++) {
                         dn = fmin(fmax(d + delta, dmin), dmax);
-                        build_K(W.D, nm, ld, dn, g, W.K, b);
+                        build_K(W.D, nm, ld, dn, g, W.K, S.etab, b);
                         if (llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &ln, &psin, b) &&
                             (short_newton || ln >= l)) {
                             accepted = true;
@@ -446,7 +461,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     }
                     if (!accepted) {
                         // restore K, L, a at the current d
-                        build_K(W.D, nm, ld, d, g, W.K, b);
+                        build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
                         llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b);
                         break;
                     }
@@ -454,7 +469,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     d = dn;
                     l = ln;
                     psi = psin;
-                    dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
+                    dr = llik_derivs(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
                     if (step < 1e-10 * d) break;
                 }
             }
@@ -483,6 +498,7 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
+    for (int i = threadIdx.x; i < 64; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     __shared__ double red[GP_WARPS];
@@ -500,12 +516,12 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
             const double d = dv[loc], g = a.g, d2 = d * d;
             for (int i = b.tid; i < p; i += GP_THREADS) S.xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
             build_D(S.xd, nm, p, W.D, ld, b);
-            build_K(W.D, nm, ld, d, g, W.K, b);
+            build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
             double l, psi;
             if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                Derivs dr = llik_derivs(W, nm, ld, d, S.a, psi, S.t1, S.t2, red, b);
+                Derivs dr = llik_derivs(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
                 // kx, kx_d = (Dx/d^2) kx ; b = K^{-1} kx (t1) by the two triangular
                 // solves (w = L^{-1} kx in t3, v = 1 + g - w^T w: no explicit
                 // inverse, no cancellation against k^T b), K'a (t2), K'b (t3)
@@ -588,7 +604,7 @@ struct GpLaunch {
 template <typename Kern>
 lagp_status prepare(lagp_ctx *ctx, const GpArgs &a, Kern kern, GpLaunch &L) {
     const int ld = (a.nmax + 31) & ~31;
-    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p) * 8 + 64;
+    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p + 64) * 8 + 64;
     if (L.smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "n_max x p too large");
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     int occ = 0;
