@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["f32bulk", "f64"], default="f32bulk")
+    ap.add_argument("--prec", choices=["f32bulk", "f64", "f64schur"], default="f32bulk")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64-plain comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -88,6 +88,14 @@ def work_per_location(n0, n, Np):
 
 def fp32_flops_per_location(n, Np, p):
     return sum((Np - j - 1) * (2 * j + 3 * p + 8) for j in range(0, n - 1))
+
+
+def fp64_schur_pass_flops_per_location(n, Np, p):
+    """FP64 flops of the FP64 Schur form's bulk pass: after step j every
+    unchosen candidate takes the dot product with the pivot column (2j), its
+    squared distance to the new point (3p), the scale by -1/d and the 20
+    flops of the table-driven exp, and the updates of u, v and r (6)."""
+    return sum((Np - j - 1) * (2 * j + 3 * p + 27) for j in range(0, n - 1))
 
 
 def fp64_flops(work, M, n, p, fused):
@@ -434,6 +442,38 @@ def run_ours(args, rank, world, local_rank):
                "speedup_f32bulk_over_f64": (M / (t_local / args.steps)) / (M / (f64_ms[0] / 1e3)),
                "identical_designs_frac": sel_same}
 
+    # the FP64 Schur (incremental O(j)) form on the same batch: the same
+    # search with its candidate state in FP64
+    f64s = None
+    if not args.no_f64 and args.prec != "f64schur":
+        s_ms, s_alc = [], []
+        L.alc_work(dev)
+        for it in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            ss, ps = step("f64schur", (a0, a1))
+            e1.record(stream)
+            barrier()
+            if it > 0:
+                s_ms.append(e0.elapsed_time(e1))
+                s_alc.append(a0.elapsed_time(a1))
+        ms_s = statistics.mean(s_ms)
+        work_s = {k: v / 3 for k, v in L.alc_work(dev).items()}
+        f64s = {"value": M / (ms_s / 1e3), "unit": "predictions/s", "ms_per_step": ms_s,
+                "alc_kernel_ms": statistics.mean(s_alc),
+                "fp64_flops_per_launch": fp64_flops(work_s, M, n, w.p, True) +
+                M * fp64_schur_pass_flops_per_location(n, Np, w.p),
+                "rmse": float(np.sqrt(np.mean((ps["mean"].cpu().numpy() - w.truth) ** 2))),
+                "identical_designs_frac_vs_f32bulk":
+                    float((ss["sel"] == s["sel"]).all(dim=1).float().mean().item())}
+        if f64 is not None:
+            f64s["speedup_over_f64_plain"] = f64["ms_per_step"] / ms_s
+            f64s["identical_designs_frac_vs_f64_plain"] = float(
+                (ss["sel"] == s64["sel"]).all(dim=1).float().mean().item())
+
     # end to end through the public host-buffer call (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -483,6 +523,10 @@ def run_ours(args, rank, world, local_rank):
                 "fp32_screen": {"achieved": fl32 / alc_avg / 1e12, "peak": fp32_peak,
                                 "frac": fl32 / alc_avg / 1e12 / fp32_peak, "unit": "TFLOP/s",
                                 "flops_per_launch": fl32}}
+    if f64s is not None:
+        a64 = f64s["fp64_flops_per_launch"] / (f64s["alc_kernel_ms"] / 1e3) / 1e12
+        f64s["roofline"] = {"bound": "alu", "kernel": "alc_bulk_kernel (FP64 state)", "unit": "TFLOP/s",
+                            "achieved": a64, "peak": fp64_peak, "frac": a64 / fp64_peak}
     cpu = None
     if not args.no_cpu and world == 1:
         S = 1024
@@ -502,6 +546,7 @@ def run_ours(args, rank, world, local_rank):
         "alc_kernel_ms": 1e3 * alc_avg,
         "rmse_vs_truth": rmse, "status_ok_frac": float((st == 0).mean()),
         "f64_plain": f64,
+        "f64_schur": f64s,
         "cuda_graph": graph_ms,
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -62,8 +62,13 @@ typedef enum { LAGP_F64 = 0, LAGP_F32 = 1 } lagp_dtype;
  *                    form of the same criterion (O(j) per candidate per
  *                    step); the leading contenders are re-scored with
  *                    Eq. (dxy) in FP64, and the partitioned-inverse update of
- *                    K_j^{-1} stays in FP64. */
-typedef enum { LAGP_PREC_F64 = 0, LAGP_PREC_F32BULK = 1 } lagp_precision;
+ *                    K_j^{-1} stays in FP64.
+ *  LAGP_PREC_F64SCHUR the same Schur-complement form with the candidate
+ *                    state in FP64 (the incremental O(j) form of the
+ *                    criterion, exact to FP64 rounding); the contenders
+ *                    within a margin of 1e-5 of the best score are
+ *                    re-scored with Eq. (dxy) as above. */
+typedef enum { LAGP_PREC_F64 = 0, LAGP_PREC_F32BULK = 1, LAGP_PREC_F64SCHUR = 2 } lagp_precision;
 
 typedef struct lagp_ctx lagp_ctx;
 
@@ -175,7 +180,7 @@ lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dt
  *   n           M final design sizes (n0 <= n[m] <= Nprime[m]), or NULL
  *               (all = n_max)
  *   d           M lengthscales (> 0);  g  nugget (>= 0)
- *   prec        LAGP_PREC_F64 or LAGP_PREC_F32BULK (see lagp_precision)
+ *   prec        LAGP_PREC_F64, LAGP_PREC_F32BULK or LAGP_PREC_F64SCHUR (see lagp_precision)
  *   sel         M x n_max int32 output: the chosen design rows in the order
  *               chosen (the n0 seeds first); -1 past n[m]
  *   alc         M x n_max FP64 output or NULL: raw Delta of Eq. (dxy) of the

@@ -1,5 +1,7 @@
-// a2..a6, FP32-bulk form: greedy ALC local design search (Fig. 1 step 2 of
-// the paper) with the candidate screen in FP32 and every decision in FP64.
+// a2..a6 in the Schur-complement (incremental) form: greedy ALC local design
+// search (Fig. 1 step 2 of the paper) with the bulk candidate state in FP32
+// (the FP32-bulk form) or in FP64 (the FP64 Schur form), and every decision
+// in FP64.
 //
 // Why not K_j^{-1} in FP32: the local matrices of these workloads are
 // ill-conditioned (cond(K_j) ~ 1e5..1e7 for nuggets 1e-4..1e-6), so the FP32
@@ -15,25 +17,26 @@
 // candidate:  u_{c,j} = (K(x_c,x*) - u_{x*}^T u_c) / lambda,
 //   v_c -= u_{c,j}^2,   r_c -= (r_{x*}/lambda) u_{c,j}.
 // The per-step contraction U^T u_{x*} is O(j) per candidate (the paper's
-// direct form is O(j^2)); its FP32 rounding error is ~j 2^-24 absolute.
+// direct form is O(j^2)); in FP32 its rounding error is ~j 2^-24 absolute,
+// in FP64 ~j 2^-53.
 //
-// Each step: FP32 scores -> contenders (FP32 score within rescore_rel of the
-// FP32 maximum, at most rescore_max, best first, ties to the lower row) ->
-// FP64 re-score of the contenders with Eq. (dxy) using FP64 K_j^{-1} ->
-// argmax (ties to the lower row) -> FP64 partitioned-inverse update of
-// K_j^{-1} (Sec. 2.2) -> FP32 recurrence with pivot x*, whose lambda and
-// r_{x*} come from the pivot's own FP32 state (self-consistent factor).
+// Each step: FP32 scores r^2 / v of the bulk state -> contenders (scores
+// within an adaptive margin of the maximum, at most rescore_max) -> FP64
+// re-score of the contenders with the three-term Eq. (dxy) against FP64
+// K_j^{-1} -> argmax (ties to the lower row) -> FP64 partitioned-inverse
+// update of K_j^{-1} (Sec. 2.2) -> the bulk recurrence with pivot x*, whose
+// lambda and r_{x*} come from the pivot's own bulk state (self-consistent
+// factor).  With FP64 state the scores differ from FP64 only by their FP32
+// rounding, so the margin floor is 1e-5 and one contender is the rule.
 //
 // Layout: one persistent CTA per location at a time (atomic work counter),
-// three CTAs per SM so that one location's serial FP64 phase overlaps other
-// locations' FP32 passes; candidate c lives in thread c / CPT, register slot
-// c % CPT (v, r, score); the whitened panel U[i][c] and the FP32 candidate
+// several CTAs per SM so that one location's serial FP64 phases overlap
+// other locations' bulk passes; candidate c lives in thread c / CPT, register
+// slot c % CPT (v, r, score); the whitened panel U[i][c] and the candidate
 // coordinates C[i][c] are per-CTA global buffers (contiguous in c, vector
-// loads, L2-resident); K_j^{-1}, k_j(x), the design coordinates and the
-// contenders' FP64 vectors sit in shared memory.  Contenders are found with
-// per-warp lists merged by one warp; each contender's FP32 column of U is
-// fetched during its FP64 re-score, so the winner's column (the next pivot)
-// is already in shared memory when the FP32 pass starts.
+// loads, L2-resident); K_j^{-1} (with a = K^{-1} k(x) and alpha = K^{-1} Y
+// beside it), k_j(x), the design coordinates and the contenders' FP64
+// vectors sit in shared memory.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -53,13 +56,28 @@ constexpr int F32_WARPS = F32_THREADS / 32;
 // FP32-vs-FP64 score error seen among the contenders re-scored so far,
 // decaying by ERR_DECAY per step (starting at ERR_INIT).
 constexpr float MARGIN_MIN = 0.02f;
+// with FP64 state the FP32 scores only round (the state is exact to FP64
+// rounding), so the margin's floor is a few FP32 ulps
+constexpr float MARGIN_MIN_F64STATE = 1e-5f;
 constexpr float MARGIN_KAPPA = 8.0f;
 constexpr float ERR_DECAY = 0.75f;
 constexpr float ERR_INIT = 0.05f;
 
-template <int CPT>
-__device__ __forceinline__ void load_vec(const float *p, float (&v)[CPT]) {
-    if constexpr (CPT % 4 == 0) {
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
+// CPT consecutive values of a candidate-indexed row (vector loads/stores)
+template <int CPT, typename T>
+__device__ __forceinline__ void load_vec(const T *p, T (&v)[CPT]) {
+    if constexpr (sizeof(T) == 4 && CPT % 4 == 0) {
 #pragma unroll
         for (int r = 0; r < CPT; r += 4) {
             float4 t = *reinterpret_cast<const float4 *>(p + r);
@@ -68,36 +86,56 @@ __device__ __forceinline__ void load_vec(const float *p, float (&v)[CPT]) {
             v[r + 2] = t.z;
             v[r + 3] = t.w;
         }
-    } else if constexpr (CPT == 2) {
-        float2 t = *reinterpret_cast<const float2 *>(p);
-        v[0] = t.x;
-        v[1] = t.y;
+    } else if constexpr (CPT % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < CPT; r += 2) {
+            typename Vec2<T>::type t = *reinterpret_cast<const typename Vec2<T>::type *>(p + r);
+            v[r] = t.x;
+            v[r + 1] = t.y;
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < CPT; r++) v[r] = p[r];
     }
 }
 
-template <int CPT>
-__device__ __forceinline__ void store_vec(float *p, const float (&v)[CPT]) {
-    if constexpr (CPT % 4 == 0) {
+template <int CPT, typename T>
+__device__ __forceinline__ void store_vec(T *p, const T (&v)[CPT]) {
+    if constexpr (sizeof(T) == 4 && CPT % 4 == 0) {
 #pragma unroll
         for (int r = 0; r < CPT; r += 4)
             *reinterpret_cast<float4 *>(p + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
-    } else if constexpr (CPT == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (CPT % 2 == 0) {
+#pragma unroll
+        for (int r = 0; r < CPT; r += 2) {
+            typename Vec2<T>::type t;
+            t.x = v[r];
+            t.y = v[r + 1];
+            *reinterpret_cast<typename Vec2<T>::type *>(p + r) = t;
+        }
     } else {
 #pragma unroll
         for (int r = 0; r < CPT; r++) p[r] = v[r];
     }
 }
 
+// K = exp(a) for the bulk state: FP32 (fast intrinsic) or FP64 (table method)
+__device__ __forceinline__ float bulk_exp(float a, const double *) { return __expf(a); }
+__device__ __forceinline__ double bulk_exp(double a, const double *etab) { return exp64_tang(a, etab); }
+
+// FP32 screening score r^2 / v from the bulk state
+__device__ __forceinline__ float bulk_score(float cov, float v, float gf) { return cov * cov / fmaxf(v, gf); }
+__device__ __forceinline__ float bulk_score(double cov, double v, float gf) {
+    const float c = (float)cov;
+    return c * c / fmaxf((float)v, gf);
+}
+
 struct F32Params {
     AlcArgs a;
     int *counter;
     unsigned long long *work;  // 4 counters: locations, sum ncon, sum ncon*j, sum ncon*j^2
-    float *U_ws;      // per CTA: nmax x Npad (whitened panel U[i][c])
-    float *C_ws;      // per CTA: p x Npad (FP32 candidate coordinates C[i][c])
+    void *U_ws;       // per CTA: nmax x Npad of T (whitened panel U[i][c])
+    void *C_ws;       // per CTA: p x Npad of T (candidate coordinates C[i][c])
     int Npad;         // F32_THREADS * CPT
     int tmax;         // rescore_max
     float rel;        // rescore_rel (cap of the contender margin)
@@ -161,9 +199,18 @@ __device__ __forceinline__ void warp_best3(float &s, int &row, int &slot) {
 
 // four resident CTAs per SM (64 registers a thread) for up to 4 candidate
 // slots a thread, fewer for the wider variants whose state needs more
-template <int CPT>
-__global__ void __launch_bounds__(F32_THREADS, CPT >= 16 ? 2 : (CPT >= 8 ? 3 : 4))
-alc_f32_kernel(F32Params P) {
+// T: the type of the bulk state (U, v, r and the candidate coordinates):
+// float for the FP32-bulk form, double for the FP64 Schur form.  Scores,
+// contenders, the re-score and the update are the same for both.
+template <typename T, int CPT>
+constexpr int bulk_min_blocks() {
+    return sizeof(T) == 8 ? (CPT >= 8 ? 1 : 2) : (CPT >= 16 ? 2 : (CPT >= 8 ? 3 : 4));
+}
+
+template <int CPT, typename T>
+__global__ void __launch_bounds__(F32_THREADS, bulk_min_blocks<T, CPT>())
+alc_bulk_kernel(F32Params P) {
+    constexpr bool F64STATE = sizeof(T) == 8;
     const AlcArgs &a = P.a;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, Npmax = a.Npmax, Npad = P.Npad, tmax = P.tmax;
@@ -185,8 +232,8 @@ alc_f32_kernel(F32Params P) {
     int *ov_slot = reinterpret_cast<int *>(ov_s + Npad);
     const size_t union_doubles =
         max((size_t)Npad, ((size_t)2 * tmax + max(F32_WARPS, tmax)) * ld);
-    float *w_u = reinterpret_cast<float *>(con_k + union_doubles);  // ld: U column of the winner
-    float *w_c = w_u + ld;                                            // p: its FP32 coordinates
+    T *w_u = reinterpret_cast<T *>(con_k + union_doubles);  // ld: U column of the winner
+    T *w_c = w_u + ld;                                        // p: its coordinates
     double *mb = cpart;
 
     __shared__ int s_loc, s_bad, s_total, s_wl;
@@ -195,11 +242,12 @@ alc_f32_kernel(F32Params P) {
     __shared__ float lst_s[LCAP], top_s[LCAP];
     __shared__ double con_kap[LCAP], con_y[LCAP], con_quad[LCAP], con_kxb[LCAP], con_yb[LCAP];
     __shared__ double s_mu, s_ex, s_ry, s_kap, s_kxb, s_dl, s_psi, s_qx;
-    __shared__ float s_vstar, s_covstar, s_err;
+    __shared__ T s_invlam, s_wnew;
+    __shared__ float s_err;
     __shared__ unsigned long long s_work[4];
 
-    float *U = P.U_ws + (size_t)blockIdx.x * nmax * Npad;
-    float *Cg = P.C_ws + (size_t)blockIdx.x * p * Npad;
+    T *U = static_cast<T *>(P.U_ws) + (size_t)blockIdx.x * nmax * Npad;
+    T *Cg = static_cast<T *>(P.C_ws) + (size_t)blockIdx.x * p * Npad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = tid * CPT;  // first candidate slot of this thread
     const int rot = blockIdx.x & (F32_WARPS - 1);
@@ -245,7 +293,8 @@ alc_f32_kernel(F32Params P) {
         for (int i = tid; i < p; i += F32_THREADS) xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
         for (int e = tid; e < p * Npad; e += F32_THREADS) {
             int i = e / Npad, c = e - i * Npad;
-            Cg[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
+            if constexpr (F64STATE) Cg[e] = c < k ? load_coord64(a.X, cands[c], p, i, a.dtype) : 0.0;
+            else Cg[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
         }
         const double inv_d64 = 1.0 / d, onepg = 1.0 + g;
         if (tid == 0) {
@@ -256,32 +305,34 @@ alc_f32_kernel(F32Params P) {
             s_work[0] += 1ull;
         }
         __syncthreads();
-        const float inv_d = (float)(1.0 / d);
-        const float gf = fmaxf((float)g, FLT_MIN);
-        float v[CPT], cov[CPT], score[CPT];
+        const T inv_d = (T)(1.0 / d);
+        const float gf = fmaxf((float)g, FLT_MIN);  // floor of v in the FP32 scores
+        const T gT = F64STATE ? (T)fmax(g, DBL_MIN) : (T)gf;
+        T v[CPT], cov[CPT];
+        float score[CPT];
         int rows[CPT];  // design rows of this thread's candidates (tie-break key)
         unsigned chosen = 0;
         {
-            float s[CPT];
+            T s[CPT];
 #pragma unroll
-            for (int r = 0; r < CPT; r++) s[r] = 0.f;
+            for (int r = 0; r < CPT; r++) s[r] = T(0);
             for (int i = 0; i < p; i++) {
-                float cv[CPT];
+                T cv[CPT];
                 load_vec<CPT>(Cg + (size_t)i * Npad + c0, cv);
-                const float qi = (float)xq[i];
+                const T qi = (T)xq[i];
 #pragma unroll
                 for (int r = 0; r < CPT; r++) {
-                    float df = cv[r] - qi;
-                    s[r] = fmaf(df, df, s[r]);
+                    T df = cv[r] - qi;
+                    s[r] = fma(df, df, s[r]);
                 }
             }
 #pragma unroll
             for (int r = 0; r < CPT; r++) {
                 const int c = c0 + r;
                 rows[r] = c < k ? cands[c] : INT32_MAX;
-                v[r] = (float)onepg;
-                cov[r] = __expf(-s[r] * inv_d);  // K(x_c, x), no nugget
-                score[r] = c < k ? cov[r] * cov[r] / v[r] : -1.f;
+                v[r] = (T)onepg;
+                cov[r] = bulk_exp(-s[r] * inv_d, etab);  // K(x_c, x), no nugget
+                score[r] = c < k ? bulk_score(cov[r], v[r], gf) : -1.f;
                 if (c >= k) chosen |= 1u << r;  // padding slots never compete
             }
         }
@@ -309,7 +360,8 @@ alc_f32_kernel(F32Params P) {
                     s_total = 1;
                 }
             } else {
-                const float margin = fminf(P.rel, fmaxf(MARGIN_MIN, MARGIN_KAPPA * s_err));
+                const float margin =
+                    fminf(P.rel, fmaxf(F64STATE ? MARGIN_MIN_F64STATE : MARGIN_MIN, MARGIN_KAPPA * s_err));
                 float gmax = w_max[0];
 #pragma unroll
                 for (int w = 1; w < F32_WARPS; w++) gmax = fmaxf(gmax, w_max[w]);
@@ -597,62 +649,66 @@ alc_f32_kernel(F32Params P) {
 #pragma unroll
             for (int r = 0; r < CPT; r++)
                 if (c0 + r == cstar) {
-                    s_vstar = v[r];
-                    s_covstar = cov[r];
+                    const T vs = v[r] > gT ? v[r] : gT;
+                    T il;
+                    if constexpr (F64STATE) il = 1.0 / sqrt(vs);
+                    else il = rsqrtf(vs);
+                    s_invlam = il;
+                    s_wnew = cov[r] * il;
                     chosen |= 1u << r;
                 }
             __syncthreads();
             if (j + 1 >= nm) break;
             // ---------------- FP32 Schur recurrence with pivot x* (new column j of U)
             {
-                const float inv_lam = rsqrtf(fmaxf(s_vstar, gf));
-                const float wnew = s_covstar * inv_lam;
-                float acc[CPT];
+                const T inv_lam = s_invlam;
+                const T wnew = s_wnew;
+                T acc[CPT];
 #pragma unroll
-                for (int r = 0; r < CPT; r++) acc[r] = 0.f;
-                const float *Ub = U + c0;
-                // loads in flight per thread: UNR rows of CPT floats
-                constexpr int UNR = CPT >= 16 ? 2 : 4;
+                for (int r = 0; r < CPT; r++) acc[r] = T(0);
+                const T *Ub = U + c0;
+                // loads in flight per thread: UNR rows of CPT values
+                constexpr int UNR = (F64STATE || CPT >= 16) ? 2 : 4;
                 int i = 0;
                 for (; i + UNR <= j; i += UNR) {
-                    float u[UNR][CPT];
+                    T u[UNR][CPT];
 #pragma unroll
                     for (int q = 0; q < UNR; q++) load_vec<CPT>(Ub + (size_t)(i + q) * Npad, u[q]);
 #pragma unroll
                     for (int q = 0; q < UNR; q++) {
-                        const float sq = w_u[i + q];
+                        const T sq = w_u[i + q];
 #pragma unroll
-                        for (int r = 0; r < CPT; r++) acc[r] = fmaf(u[q][r], sq, acc[r]);
+                        for (int r = 0; r < CPT; r++) acc[r] = fma(u[q][r], sq, acc[r]);
                     }
                 }
                 for (; i < j; i++) {
-                    float u0[CPT];
+                    T u0[CPT];
                     load_vec<CPT>(Ub + (size_t)i * Npad, u0);
-                    const float s0 = w_u[i];
+                    const T s0 = w_u[i];
 #pragma unroll
-                    for (int r = 0; r < CPT; r++) acc[r] = fmaf(u0[r], s0, acc[r]);
+                    for (int r = 0; r < CPT; r++) acc[r] = fma(u0[r], s0, acc[r]);
                 }
-                float s[CPT];
+                T s[CPT];
 #pragma unroll
-                for (int r = 0; r < CPT; r++) s[r] = 0.f;
+                for (int r = 0; r < CPT; r++) s[r] = T(0);
                 for (int ii = 0; ii < p; ii++) {
-                    float cv[CPT];
+                    T cv[CPT];
                     load_vec<CPT>(Cg + (size_t)ii * Npad + c0, cv);
-                    const float xi = w_c[ii];
+                    const T xi = w_c[ii];
 #pragma unroll
                     for (int r = 0; r < CPT; r++) {
-                        float df = cv[r] - xi;
-                        s[r] = fmaf(df, df, s[r]);
+                        T df = cv[r] - xi;
+                        s[r] = fma(df, df, s[r]);
                     }
                 }
-                float un[CPT];
+                T un[CPT];
 #pragma unroll
                 for (int r = 0; r < CPT; r++) {
-                    const float kcs = __expf(-s[r] * inv_d);  // K(x_c, x*), no nugget
+                    const T kcs = bulk_exp(-s[r] * inv_d, etab);  // K(x_c, x*), no nugget
                     un[r] = (kcs - acc[r]) * inv_lam;
-                    v[r] = fmaf(-un[r], un[r], v[r]);
-                    cov[r] = fmaf(-wnew, un[r], cov[r]);
-                    score[r] = (chosen >> r & 1u) ? -1.f : cov[r] * cov[r] / fmaxf(v[r], gf);
+                    v[r] = fma(-un[r], un[r], v[r]);
+                    cov[r] = fma(-wnew, un[r], cov[r]);
+                    score[r] = (chosen >> r & 1u) ? -1.f : bulk_score(cov[r], v[r], gf);
                 }
                 store_vec<CPT>(U + (size_t)j * Npad + c0, un);
                 float wm = -FLT_MAX;
@@ -689,51 +745,59 @@ alc_f32_kernel(F32Params P) {
     if (tid < 4 && P.work) atomicAdd(P.work + tid, s_work[tid]);
 }
 
-template <int CPT>
+template <int CPT, typename T>
 lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     cudaStream_t st = ctx->stream;
     const int Npad = F32_THREADS * CPT;
     const int tmax = ctx->tuning.rescore_max > 0 ? ctx->tuning.rescore_max : 8;
-    // dynamic shared memory, in the kernel's order (see alc_f32_kernel)
+    // dynamic shared memory, in the kernel's order (see alc_bulk_kernel)
     const size_t nmax = (size_t)a.nmax, p = (size_t)a.p;
     const size_t ld = (nmax + 3) & ~(size_t)1;
     const size_t union_doubles = std::max((size_t)Npad, (2 * (size_t)tmax + std::max(F32_WARPS, tmax)) * ld);
     const size_t smem = 8 * ((nmax + 1) * ld + ((nmax + 1) & ~(size_t)1) + nmax * p + ((p + 1) & ~(size_t)1) +
                              64 + union_doubles) +
-                        4 * (ld + p);
+                        sizeof(T) * (ld + p);
     if (smem > ctx->smem_optin)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, p too large)");
-    cudaFuncSetAttribute(alc_f32_kernel<CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(alc_bulk_kernel<CPT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f32_kernel<CPT>, F32_THREADS, smem);
-    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key("alc_f32", CPT, a.nmax, a.p, a.mean != nullptr), 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_bulk_kernel<CPT, T>, F32_THREADS, smem);
+    const bool f64state = sizeof(T) == 8;
+    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key(f64state ? "alc_f64schur" : "alc_f32", CPT, a.nmax, a.p,
+                                                    a.mean != nullptr),
+                                 f64state ? 2 : 4);
     if (occ > 0 && per_sm > occ) per_sm = occ;
     int64_t grid = (int64_t)ctx->num_sms * per_sm;
     if (grid > a.M) grid = a.M;
     if (grid < 1) grid = 1;
-    const size_t U_floats = (size_t)grid * a.nmax * Npad, C_floats = (size_t)grid * a.p * Npad;
-    float *U = static_cast<float *>(lagp_ws(ctx, WS_ALC_PANEL, (U_floats + C_floats) * 4 + 256));
+    const size_t U_elems = (size_t)grid * a.nmax * Npad, C_elems = (size_t)grid * a.p * Npad;
+    T *U = static_cast<T *>(lagp_ws(ctx, WS_ALC_PANEL, (U_elems + C_elems) * sizeof(T) + 256));
     int *counter = nullptr;
     unsigned long long *work = nullptr;
     LAGP_TRY(alc_counters(ctx, &counter, &work));
     if (!U) return LAGP_ENOMEM;
     LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    F32Params P{a, counter, work, U, U + U_floats, Npad, tmax, (float)ctx->tuning.rescore_rel};
-    alc_f32_kernel<CPT><<<(unsigned)grid, F32_THREADS, smem, st>>>(P);
+    F32Params P{a, counter, work, U, U + U_elems, Npad, tmax, (float)ctx->tuning.rescore_rel};
+    alc_bulk_kernel<CPT, T><<<(unsigned)grid, F32_THREADS, smem, st>>>(P);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
     return LAGP_OK;
 }
 
-}  // namespace
-
-lagp_status launch_alc_f32(lagp_ctx *ctx, const AlcArgs &a) {
+template <typename T>
+lagp_status launch_bulk(lagp_ctx *ctx, const AlcArgs &a) {
     if (a.nmax > 128)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: n_max above 128 is not supported");
     const int need = (a.Npmax + F32_THREADS - 1) / F32_THREADS;
-    if (need <= 1) return launch_cpt<1>(ctx, a);
-    if (need <= 2) return launch_cpt<2>(ctx, a);
-    if (need <= 4) return launch_cpt<4>(ctx, a);
-    if (need <= 8) return launch_cpt<8>(ctx, a);
-    return launch_cpt<16>(ctx, a);
+    if (need <= 1) return launch_cpt<1, T>(ctx, a);
+    if (need <= 2) return launch_cpt<2, T>(ctx, a);
+    if (need <= 4) return launch_cpt<4, T>(ctx, a);
+    if (need <= 8) return launch_cpt<8, T>(ctx, a);
+    return launch_cpt<16, T>(ctx, a);
 }
+
+}  // namespace
+
+lagp_status launch_alc_f32(lagp_ctx *ctx, const AlcArgs &a) { return launch_bulk<float>(ctx, a); }
+
+lagp_status launch_alc_f64schur(lagp_ctx *ctx, const AlcArgs &a) { return launch_bulk<double>(ctx, a); }

@@ -81,7 +81,9 @@ extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, in
     const int cpt = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
     const std::string key = prec == LAGP_PREC_F32BULK
                                 ? alc_shape_key("alc_f32", cpt, n_max, p, Y != nullptr)
-                                : alc_shape_key("alc_f64", 0, n_max, p, Y != nullptr);
+                                : prec == LAGP_PREC_F64SCHUR
+                                      ? alc_shape_key("alc_f64schur", cpt, n_max, p, Y != nullptr)
+                                      : alc_shape_key("alc_f64", 0, n_max, p, Y != nullptr);
     ctx->tuned_ctas[key] = best;
     if (best_ctas_per_sm) *best_ctas_per_sm = best;
     return LAGP_OK;

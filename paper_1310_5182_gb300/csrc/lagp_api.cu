@@ -202,12 +202,13 @@ static lagp_status alc_common(lagp_ctx *ctx, const char *fn, const void *X, int6
     if (n0 < 1 || n_max < n0 || n_max > Nprime_max || n_max > 128)
         return lagp_fail(ctx, LAGP_EINVAL, f + ": need 1 <= n0 <= n_max <= min(Nprime_max, 128)");
     if (!(g >= 0.0) || !std::isfinite(g)) return lagp_fail(ctx, LAGP_EINVAL, f + ": g must be >= 0");
-    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK)
+    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK && prec != LAGP_PREC_F64SCHUR)
         return lagp_fail(ctx, LAGP_EINVAL, f + ": unknown precision");
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
     AlcArgs a{X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0, n, n_max, d, g, sel, alc, status,
               Y, mean, s2, df};
-    return prec == LAGP_PREC_F64 ? launch_alc_f64(ctx, a) : launch_alc_f32(ctx, a);
+    return prec == LAGP_PREC_F64 ? launch_alc_f64(ctx, a)
+                                 : (prec == LAGP_PREC_F32BULK ? launch_alc_f32(ctx, a) : launch_alc_f64schur(ctx, a));
 }
 
 lagp_status lagp_alc_select(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,

@@ -198,6 +198,13 @@ def test_select_toy2d_full_config_f64(L, O):
     _select_case(L, O, W.c1_toy2d_fp64(), "f64", max_diverged=0.03)
 
 
+def test_select_toy2d_full_config_f64schur(L, O):
+    """The full 2-d configuration through the FP64 Schur (incremental O(j))
+    form: its state is FP64, so it meets the near-tie rule like the plain
+    FP64 form."""
+    _select_case(L, O, W.c1_toy2d_fp64(), "f64schur", max_diverged=0.03)
+
+
 def test_select_toy2d_full_config_f32bulk_bound(L, O):
     """The same workload through the FP32-bulk form.  Its criterion values
     (Delta ~ 1e-7 late in the search) sit at the FP32 screen's resolution, so
@@ -213,7 +220,7 @@ def test_select_toy2d_full_config_f32bulk_bound(L, O):
     assert abs(r32 - r64) <= 0.02 * r64
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
 def test_select_ragged_uneven(L, O, prec):
     """Uneven n and N' per location (several tiles of candidates, ragged tails)."""
     rng = np.random.default_rng(23)
@@ -224,13 +231,13 @@ def test_select_ragged_uneven(L, O, prec):
     _select_case(L, O, w, prec, Np_arr=Np_arr, n_arr=n_arr, max_diverged=0.05)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
 def test_select_slab3d(L, O, prec):
     w = W.slab3d(seed=8, N=30_000, grid=(4, 4, 3), n=30, Np=300)
     _select_case(L, O, w, prec, max_diverged=0.05)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
 def test_select_edge_cases(L, O, prec):
     rng = np.random.default_rng(24)
     w = W.toy2d(seed=9, N=500, M=6, Np=40, n=6)
@@ -265,7 +272,7 @@ def test_select_deterministic(L, O):
 
 # -------------------------------------------- search + fused prediction (a2..a7)
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
 def test_alc_predict_fused_matches_oracle(L, O, prec):
     """The fused entry point: its designs meet the selection rule and its
     predictions (grown by the partitioned inverse) match the oracle's
@@ -369,7 +376,7 @@ def test_agp_host_buffers_match_oracle(L, O):
                ref["d"], w.g)
 
 
-@pytest.mark.parametrize("prec", ["f32bulk", "f64"])
+@pytest.mark.parametrize("prec", ["f32bulk", "f64", "f64schur"])
 def test_agp_two_stage(L, O, prec):
     """Fig. 1 step 4 with two rounds: search at d0, MLE, search again at the
     local estimates, MLE from them, predict.  Each stage is checked against
@@ -403,7 +410,7 @@ def test_agp_two_stage(L, O, prec):
     np.testing.assert_array_equal(out["s2"], pr["s2"].cpu().numpy())
 
 
-@pytest.mark.parametrize("prec", ["f32bulk", "f64"])
+@pytest.mark.parametrize("prec", ["f32bulk", "f64", "f64schur"])
 def test_borehole_full_size_sampled(L, O, prec):
     """The full 8-d borehole configuration (N=100,000, M=10,000, (6, 50, 1000),
     d=2, g=1e-6) run whole on the GPU, exactly as the benchmark launches it;
