@@ -275,6 +275,72 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None):
             "rmse_vs_truth": float(np.sqrt(np.mean((mean[ok] - w.truth[ok]) ** 2)))}
 
 
+def alc_eval_sweep(L, dev, flush, ns=range(16, 513, 4), Nc=60_000, oracle_ns=(16, 64, 128, 256),
+                   cpu=True):
+    """Sec. 4.1's measurement: the ALC criterion of N' = 60,000 candidates at
+    one location for local designs of n = 16..512 (steps of 4), here on a
+    2-d toy design of 100,000 points (d = 0.5, g = 1e-4): the design is the
+    n nearest neighbours of the location, the candidates the 60,000 after the
+    first 512 (inputs ordered by a numpy argsort of the squared distances).
+    The factorisation of K_n (one CTA) is timed apart from the
+    candidates' evaluation, as the paper times the ALC computation with the
+    matrices given.  FP64 flops per candidate: n^2 (the triangular solve) +
+    n (3p + 21) (kernel values) + 4n (s, q) + 10."""
+    import torch
+    w = W.toy2d(seed=0, N=100_000, M=1)
+    d2 = ((w.X - w.Xref[0]) ** 2).sum(1)
+    idx = np.argsort(d2, kind="stable")[:512 + Nc].astype(np.int32)
+    X = torch.from_numpy(w.X).to(dev)
+    design_all = torch.from_numpy(idx[:512].copy()).to(dev)
+    cands = torch.from_numpy(idx[512:].copy()).to(dev)
+    x = torch.from_numpy(w.Xref[0].copy()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    rows, total = [], {}
+    for n in ns:
+        des = design_all[:n]
+        L.lagp_alc_eval(X, x, des, cands[:1], w.d, w.g)  # warm
+        ts, tp = [], []
+        for _ in range(3):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            L.lagp_alc_eval(X, x, des, cands[:0], w.d, w.g)  # the factorisation alone
+            e[1].record(stream)
+            e[2].record(stream)
+            delta, st = L.lagp_alc_eval(X, x, des, cands, w.d, w.g)
+            e[3].record(stream)
+            torch.cuda.synchronize(dev)
+            tp.append(e[0].elapsed_time(e[1]))
+            ts.append(e[2].elapsed_time(e[3]) - e[0].elapsed_time(e[1]))
+        ms = statistics.median(ts)
+        rows.append((n, ms, statistics.median(tp)))
+    p = w.p
+    flops = lambda n: Nc * (n * n + n * (3 * p + 21) + 4 * n + 10)
+    out = {"workload": "toy2d_N100000_one_location_Nprime60000", "Nprime": Nc,
+           "n": [r[0] for r in rows], "eval_ms": [r[1] for r in rows], "prep_ms": [r[2] for r in rows],
+           "cand_evals_per_sec": [Nc / (r[1] / 1e3) for r in rows],
+           "fp64_tflops": [flops(r[0]) / (r[1] / 1e3) / 1e12 for r in rows]}
+    if cpu:
+        # CPU baseline: the oracle on one core (the paper compares one CPU
+        # core), on 2,000 of the candidates
+        from oracle import oracle as O
+        O.build()
+        O.set_threads(1)
+        orc = {}
+        sub = idx[512:512 + 2000]
+        for n in oracle_ns:
+            t0 = time.perf_counter()
+            O.alc_scores(w.X, w.Xref[0], idx[:n], sub, w.d, w.g)
+            orc[n] = len(sub) / (time.perf_counter() - t0)
+        O.set_threads(os.cpu_count() or 1)
+        out["cpu_baseline"] = {"kind": "oracle", "cores": 1, "unit": "candidate evaluations/s",
+                               "sample": "2,000 of the candidates at each listed n",
+                               "value_by_n": orc,
+                               "gpu_speedup_by_n": {n: out["cand_evals_per_sec"][out["n"].index(n)] / v
+                                                    for n, v in orc.items() if n in out["n"]}}
+    return out
+
+
 def other_configs(L, dev, args, flush):
     out = {}
     w1 = W.c1_toy2d_fp64()
@@ -494,8 +560,10 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": 4 * M * 8 + 4 * M * 4}
 
     configs = None
+    e1 = None
     if not args.no_configs and world == 1:
         configs = other_configs(L, dev, args, flush)
+        e1 = alc_eval_sweep(L, dev, flush, cpu=not args.no_cpu)
     if rank != 0:
         return
     E = work_per_location(n0, n, Np)
@@ -552,6 +620,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
         "configs": configs,
+        "alc_eval_one_location": e1,
     }
     print(json.dumps(line), flush=True)
 

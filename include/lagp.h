@@ -230,6 +230,27 @@ lagp_status lagp_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_t N,
                          const int32_t *n, int32_t n_max, const double *d, double g,
                          double *mean, double *s2, double *df, int32_t *status);
 
+/* ------------------------------- a4/a5 for one location and a fixed design
+ * The ALC criterion of Eq. (dxy) for Nc candidates at one reference location
+ * x and a given design of n rows — the computation Sec. 4.1 times (one x,
+ * N' = 60,000 candidates, n = 16..512).  Per candidate, with K_n = L L^T
+ * (FP64 Cholesky of the design's covariance, nugget g on the diagonal):
+ *   u_c = L^{-1} k_n(x_c),  s_c = |u_c|^2,  q_c = (L^{-1} k_n(x))^T u_c,
+ *   delta[c] = (K(x_c, x) - q_c)^2 / (1 + g - s_c)
+ * (Eq. (dxy) with Eq. (piedef), simplified), FP64 throughout.
+ *   X        N x p design (dtype), device
+ *   x        p FP64 coordinates of the location, device
+ *   design   n design rows (int32, device), 1 <= n <= 1024
+ *   cands    Nc candidate rows (int32, device)
+ *   delta    Nc FP64 outputs (NaN for every candidate when K_n is not
+ *            positive definite)
+ *   status   1 int32 output: LAGP_OK or LAGP_ENOTPD (K_n not positive definite)
+ * Two kernels: the factorisation of K_n (one CTA) and the candidates'
+ * triangular solves (one thread per candidate). */
+lagp_status lagp_alc_eval(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                          const double *x, const int32_t *design, int32_t n, const int32_t *cands,
+                          int64_t Nc, double d, double g, double *delta, int32_t *status);
+
 /* ------------------------------------------------------- a8: local MLE
  * Per-location Newton maximisation in d of the concentrated log-likelihood
  * of Eq. (gpk), log p(Y_n | d) = log Gamma(n/2) - (n/2) log(2 pi)

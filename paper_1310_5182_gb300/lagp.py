@@ -72,12 +72,13 @@ def _load():
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     lib.lagp_alc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lagp_alc_eval.argtypes = [P, P, I64, I32, ctypes.c_int, P, P, I32, P, I64, D, D, P, P]
     lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
-              "lagp_agp", "lagp_alc_work", "lagp_exp64_check"):
+              "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_alc_eval"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -305,6 +306,26 @@ def lagp_alc_predict(X, Y, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, 
                ctx, "lagp_alc_predict")
     out.update(sel=sel, status=status, alc=alc)
     return out
+
+
+def lagp_alc_eval(X, x, design, cands, d, g):
+    """The ALC criterion (Eq. dxy, simplified) of every candidate row at one
+    location x (p values) for the given design rows.  Returns (delta [Nc],
+    status [1])."""
+    ctx = context(X.device)
+    N, p = X.shape
+    xd = torch.as_tensor(x, dtype=torch.float64, device=X.device).contiguous()
+    if xd.numel() != p:
+        raise ValueError(f"x must have p = {p} values")
+    design = torch.as_tensor(design, dtype=torch.int32, device=X.device).contiguous()
+    cands = torch.as_tensor(cands, dtype=torch.int32, device=X.device).contiguous()
+    delta = torch.empty(cands.numel(), dtype=torch.float64, device=X.device)
+    status = torch.empty(1, dtype=torch.int32, device=X.device)
+    _check(_lib.lagp_alc_eval(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(xd, "x"),
+                              _dev(design, "design"), design.numel(), _dev(cands, "cands"), cands.numel(),
+                              float(d), float(g), _dev(delta, "delta"), _dev(status, "status")),
+           ctx, "lagp_alc_eval")
+    return delta, status
 
 
 def lagp_predict(X, Y, Xref, sel, n, d, g):

@@ -474,3 +474,30 @@ def test_borehole_1m_uneven_mle_full_size_sampled(L, O):
     ref_p = O.predict(w.X, w.Y, w.Xref[samp], sel, n_s, d_gpu, w.g)
     check_pred(pr["mean"].cpu().numpy()[samp], pr["s2"].cpu().numpy()[samp], ref_p, w.X, w.Y,
                w.Xref[samp], sel, n_s, d_gpu, w.g)
+
+
+# ------------------------------- one location, many candidates (Sec. 4.1)
+
+@pytest.mark.parametrize("n", [6, 33, 96, 200])
+def test_alc_eval_matches_oracle(L, O, n):
+    """The ALC criterion of many candidates at one location for a fixed
+    design (the computation Sec. 4.1 times), against the oracle's Eq. (dxy)
+    (its simplified value) on a 2-d toy design: the n nearest neighbours form
+    the design, the next 3,000 are the candidates."""
+    w = W.toy2d(seed=51, N=40_000, M=1)
+    idx = O.knn(w.X, w.Xref, n + 3000)[0]
+    design, cands = idx[:n], idx[n:]
+    delta, st = L.lagp_alc_eval(dev(w.X), w.Xref[0], dev(design), dev(cands), w.d, w.g)
+    assert int(st.cpu()[0]) == 0
+    d3, ds = O.alc_scores(w.X, w.Xref[0], design, cands, w.d, w.g)
+    got = delta.cpu().numpy()
+    # tolerance: relative 1e-6, or the three-term cancellation floor 16 eps/g
+    # scaled by the design's conditioning over that of a one-point design
+    A = w.X[design]
+    K = np.exp(-((A[:, None] - A[None]) ** 2).sum(-1) / w.d) + w.g * np.eye(n)
+    atol = 16 * EPS / w.g * max(1.0, np.linalg.cond(K) * w.g)
+    assert np.all(np.abs(got - ds) <= np.maximum(1e-6 * np.abs(ds), atol)), \
+        np.max(np.abs(got - ds) / np.maximum(1e-6 * np.abs(ds), atol))
+    # the argmax is the oracle's up to a near tie
+    gi, oi = int(np.argmax(got)), int(np.argmax(ds))
+    assert gi == oi or ds[oi] - ds[gi] <= max(1e-6 * abs(ds[oi]), atol)
