@@ -118,8 +118,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "b79fb987936114fb4c332b7bd29aeedfdb7a51708a7eee0a6da4bdeee2cec960",
-               "dram_bytes_per_location": (3.961646e9 + 0.669469e9) / 3040}
+ALC_TRAFFIC = {"sha256": "f6c2b5b1eb034d4d7222c820836eee1e22dbf948af55e2e475249d198141902f",
+               "dram_bytes_per_location": (4.006590e9 + 0.671316e9) / 3040}
 
 
 def alc_source_hash():
@@ -578,12 +578,14 @@ def run_ours(args, rank, world, local_rank):
     fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # 128 FP32 FMA lanes / cycle / SM
     per_launch = {k: v / args.steps for k, v in work.items()}
     fl64 = fp64_flops(per_launch, M, n, w.p, True)
+    if args.prec == "f64schur":  # the bulk pass is FP64 work too
+        fl64 += M * fp64_schur_pass_flops_per_location(n, Np, w.p)
     fl32 = M * fp32_flops_per_location(n, Np, w.p)
     achieved = fl64 / alc_avg / 1e12
     traffic = None
     if ALC_TRAFFIC["sha256"] == alc_source_hash() and ALC_TRAFFIC["dram_bytes_per_location"]:
         traffic = ALC_TRAFFIC["dram_bytes_per_location"] * M
-    roofline = {"bound": "alu", "kernel": "alc_f32_kernel", "unit": "TFLOP/s", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "alc_bulk_kernel<4, float>", "unit": "TFLOP/s", "achieved": achieved,
                 "peak": fp64_peak, "frac": achieved / fp64_peak, "traffic": traffic,
                 "peak_source": f"derived: FP64, {sms} SMs x 4 flop/cycle x {mhz:.0f} MHz (sampled)",
                 "fp64_flops_per_launch": fl64,
