@@ -251,6 +251,23 @@ lagp_status lagp_alc_eval(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, la
                           const double *x, const int32_t *design, int32_t n, const int32_t *cands,
                           int64_t Nc, double d, double g, double *delta, int32_t *status);
 
+/* --------------------------------------------- separable lengthscales
+ * Sec. 3.1 notes the separable correlation, a vector theta of lengthscales:
+ * K(x,x') = exp(-sum_i (x_i - x'_i)^2 / theta_i).  It equals the isotropic
+ * correlation with d = 1 of the inputs scaled column by column,
+ * x_i / sqrt(theta_i).  This call writes that scaling (FP64, N x p, device):
+ * the search (lagp_alc_select, lagp_alc_predict, lagp_alc_eval) and the
+ * prediction (lagp_predict) called on scaled design and locations with
+ * d = 1 evaluate the separable correlation.  The candidate sets keep coming
+ * from lagp_knn on the unscaled inputs (the N' nearest neighbours in the
+ * input space; calling it on scaled inputs gives the neighbours in the
+ * theta-scaled metric instead).  The likelihood, MLE and adjoint entry
+ * points estimate a single (isotropic) d.
+ *   X      N x p inputs (dtype), device;  theta  p lengthscales > 0, device
+ *   Xs     N x p FP64 outputs, device */
+lagp_status lagp_scale_inputs(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                              const double *theta, double *Xs);
+
 /* ------------------------------------------------------- a8: local MLE
  * Per-location Newton maximisation in d of the concentrated log-likelihood
  * of Eq. (gpk), log p(Y_n | d) = log Gamma(n/2) - (n/2) log(2 pi)

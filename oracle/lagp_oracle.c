@@ -56,8 +56,38 @@ static double sqdist(const double *a, const double *b, int p) {
     return s;
 }
 
-/* isotropic Gaussian correlation K(x,x') = exp(-||x-x'||^2 / d) (Sec. 2.1) */
+/* Separable lengthscales theta_1..theta_p (Sec. 3.1 notes the separable
+ * version of the correlation as a simple modification): when set, the
+ * correlations used by the search and the prediction are
+ *   K(x,x') = exp(-(sum_i (x_i - x'_i)^2 / theta_i) / d). */
+static int g_sep = 0;
+static double g_theta[64];
+
+int orc_set_separable(const double *theta, int p) {
+    if (!theta) {
+        g_sep = 0;
+        return ORC_OK;
+    }
+    if (p < 1 || p > 64) return ORC_EINVAL;
+    for (int i = 0; i < p; i++)
+        if (!(theta[i] > 0.0)) return ORC_EINVAL;
+    for (int i = 0; i < p; i++) g_theta[i] = theta[i];
+    g_sep = 1;
+    return ORC_OK;
+}
+
+/* Gaussian correlation: isotropic K(x,x') = exp(-||x-x'||^2 / d) (Sec. 2.1),
+ * or the separable form above */
 static double kern(const double *a, const double *b, int p, double d) {
+    if (g_sep) {
+        double s = 0.0;
+        for (int i = 0; i < p; i++) {
+            double diff = a[i] - b[i];
+            double sq = diff * diff;
+            s = s + sq / g_theta[i];
+        }
+        return exp(-s / d);
+    }
     return exp(-sqdist(a, b, p) / d);
 }
 

@@ -26,6 +26,13 @@ extern "C" {
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOTPD = 2 };
 
+/* Separable lengthscales theta[0..p-1] for the correlations of the search
+ * and the prediction (orc_alc_select, orc_alc_scores, orc_partitioned_inverse,
+ * orc_predict): K(x,x') = exp(-(sum_i (x_i - x'_i)^2 / theta_i) / d).
+ * theta = NULL returns to the isotropic form.  The kNN stays Euclidean; the
+ * likelihood, MLE and adjoint functions are isotropic only. */
+int orc_set_separable(const double *theta, int p);
+
 /* Number of OpenMP threads used by the per-location loops (1 = serial).
  * Returns the value actually in effect (1 when built without OpenMP). */
 int orc_set_threads(int nthreads);

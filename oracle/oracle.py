@@ -48,6 +48,7 @@ def _load():
         P = ctypes.c_void_p
         I64, I32, D = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_separable.argtypes = [P, ctypes.c_int]
         lib.orc_knn.argtypes = [P, I64, ctypes.c_int, P, I64, P, I32, P]
         lib.orc_alc_select.argtypes = [P, I64, ctypes.c_int, P, I64, P, P, I32, I32, P, I32, P, D,
                                        P, P, I32, P, P, P]
@@ -78,6 +79,16 @@ def _ptr(a):
 def _check(rc, what):
     if rc != ORC_OK:
         raise ValueError(f"oracle {what}: invalid arguments (code {rc})")
+
+
+def set_separable(theta=None):
+    """Separable lengthscales theta (p values) for the search and prediction
+    correlations, or None for the isotropic form (see lagp_oracle.h)."""
+    if theta is None:
+        _check(_load().orc_set_separable(None, 0), "set_separable")
+        return
+    t = _f64(np.asarray(theta, dtype=np.float64))
+    _check(_load().orc_set_separable(_ptr(t), len(t)), "set_separable")
 
 
 def set_threads(n: int) -> int:

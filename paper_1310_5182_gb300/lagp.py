@@ -73,12 +73,14 @@ def _load():
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     lib.lagp_alc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
     lib.lagp_alc_eval.argtypes = [P, P, I64, I32, ctypes.c_int, P, P, I32, P, I64, D, D, P, P]
+    lib.lagp_scale_inputs.argtypes = [P, P, I64, I32, ctypes.c_int, P, P]
     lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
-              "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_alc_eval"):
+              "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_alc_eval",
+              "lagp_scale_inputs"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -305,6 +307,21 @@ def lagp_alc_predict(X, Y, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, 
                                      _dev(out["df"], "df"), _dev(status, "status")),
                ctx, "lagp_alc_predict")
     out.update(sel=sel, status=status, alc=alc)
+    return out
+
+
+def lagp_scale_inputs(X, theta):
+    """Inputs scaled for separable lengthscales theta (p values): X_i /
+    sqrt(theta_i), FP64.  Search and predict on the scaled inputs with d = 1
+    evaluate exp(-sum_i (x_i - x'_i)^2 / theta_i)."""
+    ctx = context(X.device)
+    N, p = X.shape
+    th = torch.as_tensor(theta, dtype=torch.float64, device=X.device).contiguous()
+    if th.numel() != p:
+        raise ValueError(f"theta must have p = {p} values")
+    out = torch.empty((N, p), dtype=torch.float64, device=X.device)
+    _check(_lib.lagp_scale_inputs(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(th, "theta"),
+                                  _dev(out, "Xs")), ctx, "lagp_scale_inputs")
     return out
 
 

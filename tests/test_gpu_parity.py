@@ -501,3 +501,31 @@ def test_alc_eval_matches_oracle(L, O, n):
     # the argmax is the oracle's up to a near tie
     gi, oi = int(np.argmax(got)), int(np.argmax(ds))
     assert gi == oi or ds[oi] - ds[gi] <= max(1e-6 * abs(ds[oi]), atol)
+
+
+# -------------------------------------- separable lengthscales (Sec. 3.1)
+
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
+def test_separable_search_and_predict_match_oracle(L, O, prec):
+    """Inputs scaled by lagp_scale_inputs, searched and predicted with d = 1,
+    against the oracle's separable correlation written from its definition
+    (candidate sets: the Euclidean neighbours of the unscaled inputs)."""
+    w = W.borehole(seed=64, N=20_000, M=30, n=30, Np=300)
+    theta = np.array([0.5, 4.0, 1.0, 2.0, 8.0, 1.5, 3.0, 0.8])
+    X, Xr = dev(w.X), dev(w.Xref)
+    idx, _ = L.lagp_knn(X, Xr, 300)
+    Xs, Xrs = L.lagp_scale_inputs(X, theta), L.lagp_scale_inputs(Xr, theta)
+    out = L.lagp_alc_select(Xs, Xrs, idx, 6, 30, 1.0, w.g, prec=prec)
+    sel = out["sel"].cpu().numpy()
+    O.set_separable(theta)
+    try:
+        ref = O.alc_select(w.X, w.Xref, idx.cpu().numpy(), 6, 30, 1.0, w.g, topk=4)
+        div = compare_selection(sel, ref, np.full(w.M, 30), 6, w.g)
+        assert len(div) <= 0.05 * w.M
+        pr = L.lagp_predict(Xs, dev(w.Y), Xrs, out["sel"], 30, 1.0, w.g)
+        ref_p = O.predict(w.X, w.Y, w.Xref, sel, 30, 1.0, w.g)
+    finally:
+        O.set_separable(None)
+    sc = 1.0 / np.sqrt(theta)
+    check_pred(pr["mean"].cpu().numpy(), pr["s2"].cpu().numpy(), ref_p, w.X * sc, w.Y, w.Xref * sc,
+               sel, np.full(w.M, 30), 1.0, w.g)

@@ -257,6 +257,73 @@ def test_mle_finds_grid_maximum(orc):
             assert r["d2llik"][m] < 0
 
 
+# ----------------------------------------- separable lengthscales (Sec. 3.1)
+
+def ksep(A, B, theta, d=1.0):
+    A, B = np.asarray(A, float), np.asarray(B, float)
+    return np.exp(-(((A[:, None, :] - B[None, :, :]) ** 2) / theta).sum(-1) / d)
+
+
+def test_separable_alc_equals_bruteforce_variance_reduction(orc):
+    # with theta set, Eq. (dxy) must equal v_j - v_{j+1} of Eq. (newv) for the
+    # separable correlation, recomputed here by direct solves
+    rng = np.random.default_rng(61)
+    X = rng.uniform(0, 1, (80, 3))
+    x = rng.uniform(0, 1, 3)
+    theta = np.array([0.05, 0.4, 2.0])
+    g = 1e-3
+    design = np.arange(9, dtype=np.int32)
+    cands = np.arange(9, 80, dtype=np.int32)
+    orc.set_separable(theta)
+    try:
+        d3, ds = orc.alc_scores(X, x, design, cands, 1.0, g)
+    finally:
+        orc.set_separable(None)
+
+    def v(rows):
+        K = ksep(X[rows], X[rows], theta) + g * np.eye(len(rows))
+        k = ksep(X[rows], x[None], theta)[:, 0]
+        return 1 + g - k @ np.linalg.solve(K, k)
+
+    bf = np.array([v(design) - v(np.append(design, c)) for c in cands])
+    np.testing.assert_allclose(d3, bf, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(ds, bf, rtol=1e-9, atol=1e-12)
+
+
+def test_separable_equal_lengthscales_is_isotropic(orc):
+    # theta_i = c for every i is the isotropic correlation with d c
+    w = W.borehole(seed=62, N=3_000, M=3, n=15, Np=120)
+    idx = orc.knn(w.X, w.Xref, 120)
+    iso = orc.alc_select(w.X, w.Xref, idx, 6, 15, 2.0, w.g)
+    orc.set_separable(np.full(8, 4.0))
+    try:
+        sep = orc.alc_select(w.X, w.Xref, idx, 6, 15, 0.5, w.g)
+    finally:
+        orc.set_separable(None)
+    assert np.array_equal(iso["sel"], sep["sel"])
+    np.testing.assert_allclose(sep["alc"][:, 6:], iso["alc"][:, 6:], rtol=1e-9)
+
+
+def test_separable_coordinate_scaling_invariance(orc):
+    # scaling input column i by s_i and theta_i by s_i^2 leaves the
+    # correlations, hence the search and the prediction, unchanged
+    w = W.borehole(seed=63, N=3_000, M=3, n=15, Np=120)
+    theta = np.linspace(0.5, 4.0, 8)
+    sc = np.linspace(0.2, 3.0, 8)
+    idx = orc.knn(w.X, w.Xref, 120)
+    orc.set_separable(theta)
+    try:
+        a = orc.alc_select(w.X, w.Xref, idx, 6, 15, 1.0, w.g)
+        pa = orc.predict(w.X, w.Y, w.Xref, a["sel"], 15, 1.0, w.g)
+        orc.set_separable(theta * sc ** 2)
+        b = orc.alc_select(w.X * sc, w.Xref * sc, idx, 6, 15, 1.0, w.g)
+        pb = orc.predict(w.X * sc, w.Y, w.Xref * sc, b["sel"], 15, 1.0, w.g)
+    finally:
+        orc.set_separable(None)
+    assert np.array_equal(a["sel"], b["sel"])
+    np.testing.assert_allclose(pa["mean"], pb["mean"], rtol=1e-8)
+
+
 def test_two_stage_full_gp_special_case(orc):
     # n = N' = N: the design of every round is the whole design whatever d, so
     # the second round of Fig. 1 steps 2-3 (step 4) leaves d at the first
