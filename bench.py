@@ -118,8 +118,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "f6c2b5b1eb034d4d7222c820836eee1e22dbf948af55e2e475249d198141902f",
-               "dram_bytes_per_location": (4.006590e9 + 0.671316e9) / 3040}
+ALC_TRAFFIC = {"sha256": "4449807ea8517000bebc11bbcce3241b35550879fa7c21faffb1bf3d06af7145",
+               "dram_bytes_per_location": (3.828194e9 + 0.665752e9) / 3040}
 
 
 def alc_source_hash():

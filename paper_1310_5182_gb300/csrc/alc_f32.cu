@@ -137,6 +137,7 @@ struct F32Params {
     void *U_ws;       // per CTA: nmax x Npad of T (whitened panel U[i][c])
     void *C_ws;       // per CTA: p x Npad of T (candidate coordinates C[i][c])
     int Npad;         // F32_THREADS * CPT
+    int num_sms;      // the co-resident CTAs of an SM are blockIdx.x, + num_sms, + 2 num_sms, ...
     int tmax;         // rescore_max
     float rel;        // rescore_rel (cap of the contender margin)
 };
@@ -241,6 +242,9 @@ alc_bulk_kernel(F32Params P) {
     __shared__ int lst_slot[LCAP], lst_row[LCAP], top_slot[LCAP], top_row[LCAP];
     __shared__ float lst_s[LCAP], top_s[LCAP];
     __shared__ double con_kap[LCAP], con_y[LCAP], con_quad[LCAP], con_kxb[LCAP], con_yb[LCAP];
+    __shared__ double con_mu[LCAP], con_dl[LCAP], con_ry[LCAP];
+    __shared__ long long con_key[LCAP];
+    __shared__ float con_err[LCAP];
     __shared__ double s_mu, s_ex, s_ry, s_kap, s_kxb, s_dl, s_psi, s_qx;
     __shared__ T s_invlam, s_wnew;
     __shared__ float s_err;
@@ -250,7 +254,12 @@ alc_bulk_kernel(F32Params P) {
     T *Cg = static_cast<T *>(P.C_ws) + (size_t)blockIdx.x * p * Npad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = tid * CPT;  // first candidate slot of this thread
-    const int rot = blockIdx.x & (F32_WARPS - 1);
+    // warp roles rotate with the CTA's residency slot on its SM (the CTAs
+    // sharing an SM are blockIdx.x = i, i + num_sms, ...), so that the
+    // co-resident CTAs' serial FP64 phases run on different sub-partitions
+    // (warp w runs on sub-partition w mod 4)
+    const int rot = (blockIdx.x / P.num_sms) & 3;
+    const int lead = 32 * rot;  // the thread with the CTA's scalar duties
     if (tid < 64) etab[tid] = exp64_table_g[tid];
     if (tid < 4) s_work[tid] = 0ull;
 
@@ -353,7 +362,7 @@ alc_bulk_kernel(F32Params P) {
             // the last update before everything below.
             __syncthreads();
             if (j < a.n0) {
-                if (tid == 0) {
+                if (tid == lead) {
                     lst_slot[0] = j;  // Fig. 1 step 2(a): nearest neighbours in order
                     lst_row[0] = cands[j];
                     lst_s[0] = 0.f;
@@ -529,28 +538,35 @@ alc_bulk_kernel(F32Params P) {
                 acc = warp_sum(acc);
                 if (lane == 0) con_quad[w] = acc;
             }
+            // per-contender scalars of Eqs. (piedef), (dxy), by the warp that
+            // summed the contender's quadratic form (in parallel across
+            // contenders; a^T k and alpha^T k came from other lanes of the warp)
+            __syncwarp();
+            for (int w = we; w < ncon; w += F32_WARPS) {
+                if (lane != 0) continue;
+                const double quad = con_quad[w], kxb = con_kxb[w], kap = con_kap[w];
+                const double minv = onepg - quad;  // m_j^{-1}(x_c)
+                const double m = 1.0 / minv;
+                const double kxg = -m * kxb;       // k_j(x)^T g_j(x_c)
+                const double dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
+                const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
+                con_key[w] = valid ? order_key(dl) : INT64_MIN;
+                con_mu[w] = m;
+                con_dl[w] = dl;
+                if (fused) con_ry[w] = con_y[w] - con_yb[w];  // y - Y^T K^{-1} k
+                con_err[w] = (j >= a.n0 && minv > 0.0 && dl > 0.0) ? fabsf(cs32[w] / (float)dl - 1.f) : 0.f;
+            }
             __syncthreads();
-            // R4: per-contender scalars of Eqs. (piedef), (dxy) in the lanes of
-            // warp 0, the winner (largest FP64 value, ties to the lower row),
-            // and mu b of the winner for the update
-            if (warp == 0) {
+            // R4: the winner (largest FP64 value, ties to the lower row) by
+            // integer keys in the lanes of the lead warp, and mu b of the winner
+            if (warp == rot) {
                 long long key = INT64_MIN;
                 int row = INT32_MAX;
                 float err = 0.f;
-                double m = 0.0, kxb = 0.0, kap = 0.0, ry = 0.0, dl = 0.0;
                 if (lane < ncon) {
-                    const double quad = con_quad[lane];
-                    kxb = con_kxb[lane];
-                    kap = con_kap[lane];
-                    const double minv = onepg - quad;  // m_j^{-1}(x_c)
-                    m = 1.0 / minv;
-                    const double kxg = -m * kxb;       // k_j(x)^T g_j(x_c)
-                    dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
-                    const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
-                    key = valid ? order_key(dl) : INT64_MIN;
+                    key = con_key[lane];
                     row = crow[lane];
-                    if (fused) ry = con_y[lane] - con_yb[lane];  // y - Y^T K^{-1} k
-                    err = (j >= a.n0 && minv > 0.0 && dl > 0.0) ? fabsf(cs32[lane] / (float)dl - 1.f) : 0.f;
+                    err = con_err[lane];
                 }
                 int wl = lane;
                 long long bk = key;
@@ -567,19 +583,20 @@ alc_bulk_kernel(F32Params P) {
                     }
                     err = fmaxf(err, __shfl_xor_sync(LAGP_FULL_MASK, err, o));
                 }
-                const double mu = __shfl_sync(LAGP_FULL_MASK, m, wl);
+                const double mu = con_mu[wl];
                 const double *b = con_b + (size_t)wl * ld;
                 for (int t = lane; t < j; t += 32) mb[t] = mu * b[t];
-                if (lane == wl) {
+                if (lane == 0) {
+                    const double kap = con_kap[wl], kxb = con_kxb[wl];
                     s_wl = wl;
-                    s_mu = m;
+                    s_mu = mu;
                     s_kap = kap;
                     s_kxb = kxb;
-                    s_ex = m * (kap - kxb);  // new entry of a = K^{-1} k(x)
-                    s_ry = ry;
-                    s_dl = dl;
+                    s_ex = mu * (kap - kxb);  // new entry of a = K^{-1} k(x)
+                    s_ry = fused ? con_ry[wl] : 0.0;
+                    s_dl = con_dl[wl];
                     if (j >= a.n0) s_err = fmaxf(ERR_DECAY * s_err, err);
-                    if (key == INT64_MIN) s_bad = LAGP_ENOTPD;
+                    if (bk == INT64_MIN) s_bad = LAGP_ENOTPD;
                     s_work[1] += (unsigned long long)ncon;
                     s_work[2] += (unsigned long long)ncon * j;
                     s_work[3] += (unsigned long long)ncon * j * j;
@@ -622,7 +639,7 @@ alc_bulk_kernel(F32Params P) {
                     Kt[j + 1] = fma(-ex, b[t], a_old);          // a - e_x b
                     if (fused) Kt[j + 2] = fma(-ry, mb[t], al_old);  // alpha - mu r_y b
                 }
-                if (tid == 0) {
+                if (tid == lead) {
                     const double mu = s_mu;
                     double *Kj = Kinv + (size_t)j * ld;
                     Kj[j] = mu;
@@ -642,7 +659,7 @@ alc_bulk_kernel(F32Params P) {
                     s_total = 0;
                 }
             }
-            // The FP32 recurrence continues from the pivot's own FP32 state:
+            // The bulk recurrence continues from the pivot's own bulk state:
             // lambda^2 = v_{x*} and r_{x*}, so that U stays the Cholesky factor
             // of one (slightly perturbed) matrix; mixing in the FP64 values
             // breaks that consistency and the recurrence drifts.
@@ -777,7 +794,7 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     LAGP_TRY(alc_counters(ctx, &counter, &work));
     if (!U) return LAGP_ENOMEM;
     LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    F32Params P{a, counter, work, U, U + U_elems, Npad, tmax, (float)ctx->tuning.rescore_rel};
+    F32Params P{a, counter, work, U, U + U_elems, Npad, ctx->num_sms, tmax, (float)ctx->tuning.rescore_rel};
     alc_bulk_kernel<CPT, T><<<(unsigned)grid, F32_THREADS, smem, st>>>(P);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
