@@ -488,10 +488,11 @@ alc_bulk_kernel(F32Params P) {
             }
             __syncthreads();
             // R2: partial contractions [K^{-1} | a | alpha]^T k_j(x_c), each
-            // contender's rows split over wpc warps.  Warps per contender: the
-            // largest power of two with ncon * wpc <= 8, so that the jobs fit
-            // the max(8, tmax) rows of cpart.
-            const int wpc = ncon >= 5 ? 1 : (ncon >= 3 ? 2 : (ncon >= 2 ? 4 : 8));
+            // contender's rows split over wpc warps (two for one or two
+            // contenders, else one).  Every split costs FP64 instructions (the
+            // partials' sums) on the unit that bounds the kernel, so the split
+            // stays small: two halves shorten the chain without costing more.
+            const int wpc = ncon >= 3 ? 1 : 2;
             if (j > 0) {
                 const int nrows = max(F32_WARPS, tmax);  // rows of cpart
                 for (int job = we; job < ncon * wpc && job < nrows; job += F32_WARPS) {
@@ -509,7 +510,7 @@ alc_bulk_kernel(F32Params P) {
                 }
             }
             __syncthreads();
-            // R3: sum of the partials (fixed pairwise order): b = K^{-1} k,
+            // R3: sum of the partials (first half + second half): b = K^{-1} k,
             // a^T k, alpha^T k; then k^T b, one warp per contender
             for (int w = we; w < ncon; w += F32_WARPS) {
                 if (j == 0) {
@@ -519,13 +520,7 @@ alc_bulk_kernel(F32Params P) {
                 const double *P0 = cpart + (size_t)w * wpc * ld;
                 double acc = 0.0;
                 for (int t = lane; t < jo; t += 32) {
-                    double bt;
-                    if (wpc == 1) bt = P0[t];
-                    else if (wpc == 2) bt = P0[t] + P0[ld + t];
-                    else if (wpc == 4) bt = (P0[t] + P0[ld + t]) + (P0[2 * ld + t] + P0[3 * ld + t]);
-                    else
-                        bt = ((P0[t] + P0[ld + t]) + (P0[2 * ld + t] + P0[3 * ld + t])) +
-                             ((P0[4 * ld + t] + P0[5 * ld + t]) + (P0[6 * ld + t] + P0[7 * ld + t]));
+                    const double bt = wpc == 1 ? P0[t] : P0[t] + P0[ld + t];
                     if (t < j) {
                         con_b[(size_t)w * ld + t] = bt;
                         acc = fma(con_k[(size_t)w * ld + t], bt, acc);
@@ -538,28 +533,28 @@ alc_bulk_kernel(F32Params P) {
                 acc = warp_sum(acc);
                 if (lane == 0) con_quad[w] = acc;
             }
-            // per-contender scalars of Eqs. (piedef), (dxy), by the warp that
-            // summed the contender's quadratic form (in parallel across
-            // contenders; a^T k and alpha^T k came from other lanes of the warp)
-            __syncwarp();
-            for (int w = we; w < ncon; w += F32_WARPS) {
-                if (lane != 0) continue;
-                const double quad = con_quad[w], kxb = con_kxb[w], kap = con_kap[w];
-                const double minv = onepg - quad;  // m_j^{-1}(x_c)
-                const double m = 1.0 / minv;
-                const double kxg = -m * kxb;       // k_j(x)^T g_j(x_c)
-                const double dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
-                const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
-                con_key[w] = valid ? order_key(dl) : INT64_MIN;
-                con_mu[w] = m;
-                con_dl[w] = dl;
-                if (fused) con_ry[w] = con_y[w] - con_yb[w];  // y - Y^T K^{-1} k
-                con_err[w] = (j >= a.n0 && minv > 0.0 && dl > 0.0) ? fabsf(cs32[w] / (float)dl - 1.f) : 0.f;
-            }
             __syncthreads();
-            // R4: the winner (largest FP64 value, ties to the lower row) by
-            // integer keys in the lanes of the lead warp, and mu b of the winner
+            // R4, in the lanes of the lead warp (one contender a lane: the FP64
+            // unit takes a warp instruction whatever the number of active lanes,
+            // so the contenders' scalars share instructions): the scalars of
+            // Eqs. (piedef), (dxy), the winner (largest FP64 value, ties to the
+            // lower row) by integer keys, and mu b of the winner
             if (warp == rot) {
+                if (lane < ncon) {
+                    const int w = lane;
+                    const double quad = con_quad[w], kxb = con_kxb[w], kap = con_kap[w];
+                    const double minv = onepg - quad;  // m_j^{-1}(x_c)
+                    const double m = 1.0 / minv;
+                    const double kxg = -m * kxb;       // k_j(x)^T g_j(x_c)
+                    const double dl = kxg * kxg * minv + 2.0 * kxg * kap + kap * kap * m;
+                    const bool valid = minv > 0.0 && dl == dl;  // positive m^{-1}, not NaN
+                    con_key[w] = valid ? order_key(dl) : INT64_MIN;
+                    con_mu[w] = m;
+                    con_dl[w] = dl;
+                    if (fused) con_ry[w] = con_y[w] - con_yb[w];  // y - Y^T K^{-1} k
+                    con_err[w] = (j >= a.n0 && minv > 0.0 && dl > 0.0) ? fabsf(cs32[w] / (float)dl - 1.f) : 0.f;
+                }
+                __syncwarp();
                 long long key = INT64_MIN;
                 int row = INT32_MAX;
                 float err = 0.f;
