@@ -86,6 +86,10 @@ typedef struct {
                                FP32-vs-FP64 score error observed on earlier
                                re-scores (decaying 0.75x per step), at least
                                0.02 and at most rescore_rel */
+    int32_t knn_path;       /* kNN collection pass (lagp_knn): 0 = automatic
+                               (tcgen05 tensor cores, FP16 split products,
+                               for p <= 20; CUDA cores otherwise), 1 = CUDA
+                               cores (FP32) always */
 } lagp_tuning;
 
 /* Create a context on CUDA device `device` that enqueues on `cuda_stream`
@@ -165,6 +169,23 @@ lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, la
 lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
                      const void *Xref, int64_t M, const int32_t *Nprime, int32_t Nprime_max,
                      int32_t *idx, int32_t *status);
+
+/* Diagnostic of the kNN screen's collection pass on the tensor cores (used
+ * by lagp_knn for p <= 20 unless tuning.knn_path = 1): out (device, M x N
+ * floats) receives, for every location m and design row r, the value
+ *   s = |y_m|^2 + |y_r|^2 - 2 y_m . y_r
+ * that the pass computes with FP16 split products and FP32 accumulation,
+ * where y = fl32(x - c) are the coordinates centred at the midrange c of
+ * each coordinate over X and Xref.  It differs from |y_m - y_r|^2 by at most
+ * the pass's error bound.  Requires 1 <= p <= 20; other arguments as lagp_knn. */
+lagp_status lagp_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                             const void *Xref, int64_t M, float *out);
+
+/* Diagnostic of the last lagp_knn call on this context: *n_retry receives
+ * the number of locations that the exact (CUDA-core, direct-form) retry of
+ * the screen recomputed, *tc_failed 1 if the tensor-core pass gave up on a
+ * bounded wait (its locations then went to the retry).  Synchronises. */
+lagp_status lagp_knn_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed);
 
 /* ---------------------------------------------- a2..a6: greedy ALC search
  * Local designs by the greedy ALC search of Fig. 1 step 2: the first n0

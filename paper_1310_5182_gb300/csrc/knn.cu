@@ -30,8 +30,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "device_util.cuh"
+#include "knn_common.cuh"
 #include "lagp_internal.h"
 
 namespace {
@@ -57,7 +59,6 @@ __host__ __device__ inline int tile_len(int ps) {
     return t > 512 ? 512 : (t < 32 ? 32 : t);
 }
 
-__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 // 16-byte asynchronous global-to-shared copy (bypassing L1), and its fences
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -68,16 +69,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 constexpr int CAND_CAP = 8192;        // candidate capacity cap (sort in shared memory)
 constexpr int SORT_THREADS = 256;
-
-// Unsigned keys with the order of the doubles (0 below every key), so that
-// zero-initialised buffers work as the identity of atomicMax.
-__device__ __forceinline__ unsigned long long dkey(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double dkey_inv(unsigned long long k) {
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
 
 // Per-coordinate bounds of the design and the reference locations:
 // kmax[i] = key of max_i, kmin[i] = ~key of min_i (both maximised).  Eight
@@ -129,25 +120,6 @@ __global__ void knn_bounds(const void *__restrict__ X, int64_t N, const void *__
         if (smax[i]) atomicMax(&kmax[i], smax[i]);
         if (smin[i]) atomicMax(&kmin[i], smin[i]);
     }
-}
-
-// Centre c_i (midrange of coordinate i) and B = max_i |x_i - c_i| (with a
-// relative slack of 2^-50 for the rounding of c_i), from the bounds of the
-// finite coordinates (a coordinate with none gets c_i = 0, B unchanged).
-__device__ void centre_and_bound(const unsigned long long *kmax, const unsigned long long *kmin,
-                                 int p, double *c, double &B) {
-    double b = 0.0;
-    for (int i = 0; i < p; i++) {
-        if (kmax[i] == 0ull) {  // no finite value in this coordinate
-            c[i] = 0.0;
-            continue;
-        }
-        const double hi = dkey_inv(kmax[i]), lo = dkey_inv(~kmin[i]);
-        const double ci = 0.5 * lo + 0.5 * hi;
-        c[i] = ci;
-        b = fmax(b, fmax(hi - ci, ci - lo) + 0x1p-52 * fmax(fabs(lo), fabs(hi)));
-    }
-    B = b * (1.0 + 0x1p-50);
 }
 
 // Centred FP32 copy of design row r, (y_0 .. y_{p-1}, |y|^2, 0 padding),
@@ -358,7 +330,7 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
            const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
            int32_t *__restrict__ cand, int32_t Cmax, int32_t *__restrict__ cand_count,
            int32_t *__restrict__ status, int64_t stride, int32_t *__restrict__ retry, int retry_pass,
-           int *__restrict__ counter) {
+           int *__restrict__ counter, float *__restrict__ tau_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pp = row_stride(p);              // floats per centred row (coordinates, norm, pad)
     const int TT = tile_len(pp);               // rows per tile
@@ -409,7 +381,8 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
             for (int b = lane; b < HB; b += 32) hist[ql * HB + b] = 0;
             if (lane == 0) s_count[ql] = s_count0[ql] = 0;
         }
-        if (!__syncthreads_or(mine_any)) continue;  // nothing to do in this block
+        // a block without a query to screen skips the passes (not the results)
+        const bool any_ok = __syncthreads_or(mine_any);
         float qr[QPW][P > 0 ? P : 1] = {};
         float qn[QPW] = {};
 #pragma unroll
@@ -429,7 +402,11 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
         // exactly when s <= t rounded down to a float, so the hot loop compares
         // in FP32 (an FP64 compare per point would occupy the slow FP64 unit)
         float tau0[QPW] = {}, tau2f[QPW] = {};
-        for (int pass = 0; pass < 3; pass++) {
+        // with tau_out, passes A and B only: the sampled threshold tau0 of
+        // every query (NaN for one that is not screened) for the collection
+        // pass on the tensor cores
+        const int npass = !any_ok ? 0 : (tau_out ? 2 : 3);
+        for (int pass = 0; pass < npass; pass++) {
             // passes A, B: the sampled rows (contiguous in Ys); C: all rows
             const float *src = pass < 2 ? Ys : Y32;
             const int64_t nrows = pass < 2 ? nsamp : N;
@@ -487,6 +464,12 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
                 __syncwarp();
             }
             __syncthreads();
+        }
+        if (tau_out) {
+#pragma unroll
+            for (int h = 0; h < QPW; h++)
+                if (active[h] && lane == 0) tau_out[q[h]] = ok[h] ? tau0[h] : CUDART_NAN_F;
+            continue;
         }
 #pragma unroll
         for (int h = 0; h < QPW; h++) {
@@ -569,9 +552,13 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
          const void *__restrict__ Xref, int64_t M, const int32_t *__restrict__ Np, int32_t Npmax,
          const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
          const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_count, int32_t Cmax,
-         int32_t *__restrict__ idx) {
+         int32_t *__restrict__ idx, const float *__restrict__ tau2v, int32_t *__restrict__ retry,
+         int only_retried) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t q = blockIdx.x;
+    // only_retried: the queries that the exact retry recollected; otherwise
+    // every query but those (their rows are written by the second launch)
+    if (retry && (retry[q] != 0) != (only_retried != 0)) return;
     const int C = cand_count[q];
     const int k = Np ? Np[q] : Npmax;
     int32_t *out = idx + q * Npmax;
@@ -593,7 +580,7 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     __shared__ uint32_t hist[256];
     __shared__ int wsum[SORT_THREADS / 32];
     __shared__ uint32_t s_prefix;
-    __shared__ int s_kk, s_big;
+    __shared__ int s_kk, s_big, s_fail;
     __shared__ float s_tauf;
     __shared__ uint32_t tied[CAND_CAP / 32];
     const int ps = row_stride(p);
@@ -661,8 +648,24 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
         const float tauf = __double2float_rd(screen_margin(__uint_as_float(s_prefix), p, sB));
         s_tauf = tauf;
         s_delta2 = 2.0 * tie_bound(tauf, p, sB);
+        s_fail = 0;
+        if (tau2v) {
+            // rows collected on the tensor cores under tau2: the N'-th of them
+            // (its direct FP32 value s_prefix bounds its exact distance) must
+            // lie within the radius that tau2 guarantees collected, else the
+            // query goes to the exact retry
+            const double u = 0x1p-24 * (1.0 + 0x1p-27);
+            const double e2 = 2.0 * u * sB * sqrt((double)p);
+            const double rk = sqrt((double)__uint_as_float(s_prefix)) * pow(1.0 - u, -0.5 * (p + 4)) * (1.0 + 1e-13) + e2;
+            s_fail = !(rk <= tc_collected_radius(tau2v[q], p, tc_k(p), sB));
+        }
     }
     __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) retry[q] = 1;
+        for (int t = threadIdx.x; t < Npmax; t += SORT_THREADS) out[t] = -1;
+        return;
+    }
     const float tauf = s_tauf;
     // (3) survivors, in candidate order, as (s, row) keys
     int mine = 0;
@@ -766,23 +769,28 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     for (int t = threadIdx.x; t < Npmax; t += SORT_THREADS) out[t] = t < k ? (int32_t)(uint32_t)sk[t] : -1;
 }
 
+// The screen's first launch: the sampled threshold and the collection on the
+// norm expansion (CUDA cores), or with tau0 the sampled threshold only (the
+// collection then runs on the tensor cores); and the exact retry of the
+// flagged queries on the direct form.
 template <int P>
-void launch_screen(dim3 grid, size_t smem, cudaStream_t st, const float *Y32, const float *Ys,
-                   int64_t N, int p,
-                   const void *Xref, lagp_dtype dt, int64_t M, const int32_t *Np, int32_t Npmax,
-                   const unsigned long long *kmax, const unsigned long long *kmin, int32_t *cand,
-                   int32_t Cmax, int32_t *cc, int32_t *status, int64_t stride, int32_t *retry,
-                   int *counters) {
-    cudaFuncSetAttribute(knn_screen<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(knn_screen<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // sampled threshold on the norm expansion, then the exact retry of the
-    // flagged queries on the direct form
-    knn_screen<P, true><<<grid, SCREEN_THREADS, smem, st>>>(Y32, Ys, N, p, Xref, dt, M, Np, Npmax, kmax, kmin,
-                                                            cand, Cmax, cc, status, stride, retry, 0,
-                                                            counters);
-    knn_screen<P, false><<<grid, SCREEN_THREADS, smem, st>>>(Y32, Y32, N, p, Xref, dt, M, Np, Npmax, kmax,
-                                                             kmin, cand, Cmax, cc, status, 1, retry, 1,
-                                                             counters + 1);
+void launch_screen(lagp_ctx *ctx, bool retry_pass, dim3 grid, size_t smem, const float *Y32, const float *Ys,
+                   int64_t N, int p, const void *Xref, lagp_dtype dt, int64_t M, const int32_t *Np, int32_t Npmax,
+                   const unsigned long long *kmax, const unsigned long long *kmin, int32_t *cand, int32_t Cmax,
+                   int32_t *cc, int32_t *status, int64_t stride, int32_t *retry, int *counters, float *tau0) {
+    cudaStream_t st = ctx->stream;
+    if (!retry_pass) {
+        cudaFuncSetAttribute(knn_screen<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        knn_screen<P, true><<<grid, SCREEN_THREADS, smem, st>>>(Y32, Ys, N, p, Xref, dt, M, Np, Npmax, kmax, kmin,
+                                                                cand, Cmax, cc, status, stride, retry, 0,
+                                                                counters, tau0);
+    } else {
+        cudaFuncSetAttribute(knn_screen<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        knn_screen<P, false><<<grid, SCREEN_THREADS, smem, st>>>(Y32, Y32, N, p, Xref, dt, M, Np, Npmax, kmax,
+                                                                 kmin, cand, Cmax, cc, status, 1, retry, 1,
+                                                                 counters + 1, nullptr);
+    }
+    ctx->launches++;
 }
 
 }  // namespace
@@ -791,9 +799,11 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
                        const void *Xref, int64_t M, const int32_t *Np, int32_t Npmax,
                        int32_t *idx, int32_t *status) {
     cudaStream_t st = ctx->stream;
+    ctx->knn_last_M = M;
     const int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
-    // meta: two block counters (offset 64), the coordinate bounds (offsets 256
-    // and 768, 64 keys each), then per-query candidate counts and retry flags
+    // meta: the tensor-core screen's failure word (offset 0), two block
+    // counters (offset 64), the coordinate bounds (offsets 256 and 768, 64
+    // keys each), then per-query candidate counts and retry flags
     constexpr size_t META_HEAD = 1280;
     char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
     int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
@@ -817,28 +827,99 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
                                      nsamp_pad, stride);
     ctx->launches += 2;
     LAGP_CUDA(ctx, cudaGetLastError());
+    // collection on the tensor cores unless the tuning asks for CUDA cores
+    void *tc_ws = nullptr;
+    float *tau0 = nullptr, *tau2 = nullptr;
+    if (ctx->tuning.knn_path == 0 && knn_tc_supported(p)) {
+        tc_ws = lagp_ws(ctx, WS_KNN_TC, knn_tc_workspace(N, M, p));
+        if (!tc_ws) return LAGP_ENOMEM;
+        LAGP_TRY(launch_knn_tc_prep(ctx, tc_ws, X, N, p, dtype, Xref, M, kmax, kmin, &tau0, &tau2));
+    }
+    int *tc_err = reinterpret_cast<int *>(meta);
 
     size_t smem = (size_t)QB * HB * 4 + 2 * (size_t)tile_len(pp) * pp * 4 + (size_t)QB * pp * 4;
     // persistent grid: two CTAs per SM, blocks of QB queries from a counter
     const int64_t nblk = (M + QB - 1) / QB;
     dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)ctx->num_sms * 2));
-    switch (p) {
-        case 2: launch_screen<2>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
-        case 3: launch_screen<3>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
-        case 8: launch_screen<8>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
-        default: launch_screen<0>(grid, smem, st, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters); break;
-    }
-    ctx->launches += 2;
-    LAGP_CUDA(ctx, cudaGetLastError());
-
     int Cp = 1;
     while (Cp < Cmax) Cp <<= 1;
     size_t smem_sort = (size_t)Cp * 16;
     if (smem_sort > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: N' too large for the sort");
     cudaFuncSetAttribute(knn_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sort);
-    knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Y32, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
-                                                           cand, cc, Cmax, idx);
+    auto screen = [&](bool retry_pass) {
+        switch (p) {
+            case 2: launch_screen<2>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
+            case 3: launch_screen<3>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
+            case 8: launch_screen<8>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
+            default: launch_screen<0>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
+        }
+    };
+    auto sort = [&](const float *tau2v, int32_t *rflags, int only_retried) {
+        knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Y32, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
+                                                               cand, cc, Cmax, idx, tau2v, rflags, only_retried);
+        ctx->launches++;
+    };
+    screen(false);
+    LAGP_CUDA(ctx, cudaGetLastError());
+    if (tc_ws) {
+        // collection on the tensor cores, the sort (which checks each query's
+        // collection), the exact retry of the flagged queries and their sort
+        LAGP_TRY(launch_knn_tc_collect(ctx, tc_ws, N, p, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, retry,
+                                       tc_err, tau2, nullptr));
+        sort(tau2, retry, 0);
+        screen(true);
+        sort(nullptr, retry, 1);
+    } else {
+        screen(true);
+        sort(nullptr, nullptr, 0);
+    }
+    LAGP_CUDA(ctx, cudaGetLastError());
+    return LAGP_OK;
+}
+
+// Diagnostic: the tensor-core values s of every (query, design row) pair, as
+// the collection pass computes them (out: M x N floats).
+lagp_status launch_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtype dtype,
+                               const void *Xref, int64_t M, float *out) {
+    if (!knn_tc_supported(p)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn_tc_dist: p > 20");
+    cudaStream_t st = ctx->stream;
+    constexpr size_t META_HEAD = 1280;
+    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
+    void *tc_ws = lagp_ws(ctx, WS_KNN_TC, knn_tc_workspace(N, M, p));
+    if (!meta || !tc_ws) return LAGP_ENOMEM;
+    unsigned long long *kmax = reinterpret_cast<unsigned long long *>(meta + 256);
+    unsigned long long *kmin = reinterpret_cast<unsigned long long *>(meta + 768);
+    int32_t *cc = reinterpret_cast<int32_t *>(meta + META_HEAD);
+    int32_t *retry = cc + M;
+    LAGP_CUDA(ctx, cudaMemsetAsync(meta, 0, META_HEAD, st));
+    knn_bounds<<<ctx->num_sms * 4, 256, 0, st>>>(X, N, Xref, M, p, dtype, kmax, kmin);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
+    float *tau0 = nullptr, *tau2 = nullptr;
+    LAGP_TRY(launch_knn_tc_prep(ctx, tc_ws, X, N, p, dtype, Xref, M, kmax, kmin, &tau0, &tau2));
+    return launch_knn_tc_collect(ctx, tc_ws, N, p, M, nullptr, 1, kmax, kmin, nullptr, 1, cc, nullptr, retry,
+                                 reinterpret_cast<int *>(meta), tau2, out);
+}
+
+// Diagnostic: of the last kNN call on the context, the queries that went to
+// the exact retry and whether the tensor-core pass gave up on a wait.
+lagp_status knn_last_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed) {
+    const int64_t M = ctx->knn_last_M;
+    char *meta = static_cast<char *>(ctx->ws[WS_KNN_META]);
+    if (!meta || M <= 0) {
+        *n_retry = 0;
+        *tc_failed = 0;
+        return LAGP_OK;
+    }
+    constexpr size_t META_HEAD = 1280;
+    std::vector<int32_t> r((size_t)M);
+    int32_t f = 0;
+    LAGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    LAGP_CUDA(ctx, cudaMemcpy(r.data(), meta + META_HEAD + (size_t)M * 4, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    LAGP_CUDA(ctx, cudaMemcpy(&f, meta, 4, cudaMemcpyDeviceToHost));
+    int64_t n = 0;
+    for (int32_t v : r) n += v != 0;
+    *n_retry = n;
+    *tc_failed = f;
     return LAGP_OK;
 }

@@ -128,7 +128,8 @@ lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in) {
     if (!ctx || !in) return LAGP_EINVAL;
     if (in->ctas_per_sm < 0 || in->ctas_per_sm > 32 || in->block_threads < 0 ||
         in->block_threads > 1024 || (in->block_threads % 32) != 0 || in->rescore_max < 1 ||
-        in->rescore_max > 32 || !(in->rescore_rel >= 0.0) || !(in->rescore_rel < 1.0))
+        in->rescore_max > 32 || !(in->rescore_rel >= 0.0) || !(in->rescore_rel < 1.0) ||
+        in->knn_path < 0 || in->knn_path > 1)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_set_tuning: field out of range");
     ctx->tuning = *in;
     return LAGP_OK;
@@ -179,6 +180,22 @@ lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dt
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: Nprime_max above the supported 4096");
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
     return launch_knn(ctx, X, N, p, dtype, Xref, M, Nprime, Nprime_max, idx, status);
+}
+
+lagp_status lagp_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
+                             const void *Xref, int64_t M, float *out) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->err.clear();
+    LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_knn_tc_dist"));
+    if (M < 1 || !Xref || !out) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn_tc_dist: need M >= 1, Xref, out");
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return launch_knn_tc_dist(ctx, X, N, p, dtype, Xref, M, out);
+}
+
+lagp_status lagp_knn_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed) {
+    if (!ctx || !n_retry || !tc_failed) return LAGP_EINVAL;
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return knn_last_stats(ctx, n_retry, tc_failed);
 }
 
 // --------------------------------------------------------------- ALC search

@@ -14,6 +14,7 @@ enum WsSlot {
     WS_KNN_X32 = 0,   // FP32 copy of the design for kNN screening
     WS_KNN_CAND,      // kNN per-query candidate rows
     WS_KNN_META,      // kNN per-query counters / thresholds / flags
+    WS_KNN_TC,        // kNN tensor-core operands and sampled thresholds
     WS_ALC_PANEL,     // ALC per-CTA candidate panel (F64 kernel values or F32 whitened U)
     WS_ALC_STATE,     // ALC per-CTA FP64 state (K^{-1}, vectors)
     WS_ALC_COUNTER,   // persistent-grid work counters
@@ -31,12 +32,13 @@ struct lagp_ctx {
     void *ws[WS_NSLOTS] = {};
     size_t ws_bytes[WS_NSLOTS] = {};
     std::string err;
-    lagp_tuning tuning = {0, 0, 8, 0.5};
+    lagp_tuning tuning = {0, 0, 8, 0.5, 0};
     int64_t launches = 0;
     // autotuned resident CTAs per SM, keyed by the ALC problem shape
     std::map<std::string, int> tuned_ctas;
     int tune_override = 0;  // set by the autotuner while it times a candidate
     bool work_zeroed = false;  // ALC work counters cleared once after allocation
+    int64_t knn_last_M = 0;    // queries of the last lagp_knn call (for lagp_knn_stats)
 };
 
 // Shape key of an ALC launch for the autotuner's table.
@@ -69,6 +71,20 @@ void *lagp_ws(lagp_ctx *ctx, WsSlot slot, size_t bytes);
 lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtype dtype,
                        const void *Xref, int64_t M, const int32_t *Np, int32_t Npmax,
                        int32_t *idx, int32_t *status);
+
+// kNN collection pass on the tensor cores (knn_tc.cu)
+bool knn_tc_supported(int p);
+size_t knn_tc_workspace(int64_t N, int64_t M, int p);
+lagp_status launch_knn_tc_prep(lagp_ctx *ctx, void *ws, const void *X, int64_t N, int p, lagp_dtype dtype,
+                               const void *Xref, int64_t M, const unsigned long long *kmax,
+                               const unsigned long long *kmin, float **tau0, float **tau2);
+lagp_status launch_knn_tc_collect(lagp_ctx *ctx, void *ws, int64_t N, int p, int64_t M, const int32_t *Np,
+                                  int32_t Npmax, const unsigned long long *kmax, const unsigned long long *kmin,
+                                  int32_t *cand, int32_t Cmax, int32_t *cand_count, int32_t *status,
+                                  int32_t *retry, int *err, float *tau2, float *dump);
+lagp_status launch_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtype dtype,
+                               const void *Xref, int64_t M, float *out);
+lagp_status knn_last_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed);
 
 struct AlcArgs {
     const void *X;

@@ -36,7 +36,8 @@ _STATUS = {0: "LAGP_OK", 1: "LAGP_EINVAL", 2: "LAGP_ENOTPD", 3: "LAGP_ECUDA", 4:
 
 class lagp_tuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("rescore_max", ctypes.c_int32), ("rescore_rel", ctypes.c_double)]
+                ("rescore_max", ctypes.c_int32), ("rescore_rel", ctypes.c_double),
+                ("knn_path", ctypes.c_int32)]
 
 
 def _load():
@@ -75,12 +76,14 @@ def _load():
     lib.lagp_alc_eval.argtypes = [P, P, I64, I32, ctypes.c_int, P, P, I32, P, I64, D, D, P, P]
     lib.lagp_scale_inputs.argtypes = [P, P, I64, I32, ctypes.c_int, P, P]
     lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
+    lib.lagp_knn_tc_dist.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P]
+    lib.lagp_knn_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I32)]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
               "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_alc_eval",
-              "lagp_scale_inputs"):
+              "lagp_scale_inputs", "lagp_knn_tc_dist", "lagp_knn_stats"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -252,6 +255,31 @@ def lagp_knn(X: torch.Tensor, Xref: torch.Tensor, Nprime_max: int, Nprime=None):
                              int(Nprime_max), _dev(idx, "idx"), _dev(status, "status")),
                ctx, "lagp_knn")
     return idx, status
+
+
+def lagp_knn_tc_dist(X: torch.Tensor, Xref: torch.Tensor) -> torch.Tensor:
+    """Diagnostic: the squared distances of the kNN screen's tensor-core
+    collection pass, |y_m|^2 + |y_r|^2 - 2 y_m . y_r on centred FP32
+    coordinates (FP16 split products, FP32 accumulation).  Returns [M, N]
+    float32."""
+    ctx = context(X.device)
+    N, p = X.shape
+    M = Xref.shape[0]
+    if Xref.dtype != X.dtype or Xref.shape[1] != p:
+        raise ValueError("Xref must match X in dtype and p")
+    out = torch.empty((M, N), dtype=torch.float32, device=X.device)
+    _check(_lib.lagp_knn_tc_dist(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref"), M,
+                                 _dev(out, "out")), ctx, "lagp_knn_tc_dist")
+    return out
+
+
+def knn_stats(device=None) -> dict:
+    """Of the last lagp_knn call: locations recomputed by the exact retry of
+    the screen, and whether the tensor-core pass gave up on a wait."""
+    ctx = context(device)
+    n, f = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(_lib.lagp_knn_stats(ctx, ctypes.byref(n), ctypes.byref(f)), ctx, "lagp_knn_stats")
+    return {"retried": int(n.value), "tc_failed": int(f.value)}
 
 
 def lagp_alc_select(X, Xref, idx, n0, n, d, g, prec="f32bulk", Nprime=None, n_max=None,
