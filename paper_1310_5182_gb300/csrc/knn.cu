@@ -68,6 +68,20 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 constexpr int CAND_CAP = 8192;        // candidate capacity cap (sort in shared memory)
+// kNN meta area: the tensor-core screen's failure word (offset 0), two block
+// counters (64), the coordinate bounds (256 and 768, 64 keys each), the
+// launch constants (KnnConst, 1280), then per-query candidate counts and
+// retry flags
+constexpr size_t META_HEAD = 2048;
+constexpr size_t META_CONST = 1280;
+
+// Constants of one kNN launch, written once by knn_prep: the centre c and
+// half-width B of the coordinates, e2 = 2uB sqrt(p) and the power bounds
+// g_half >= (1 + u)^((p+4)/2), (1 - u)^(-(p+4)/2) and g_full >= (1 + u)^(p+4).
+struct KnnConst {
+    double c[64];
+    double B, e2, g_half, g_full;
+};
 constexpr int SORT_THREADS = 256;
 
 // Per-coordinate bounds of the design and the reference locations:
@@ -136,15 +150,31 @@ __device__ __forceinline__ void centred_row(const void *X, int64_t N, int64_t r,
     for (int i = p; i < ps; i++) out[i] = i == p ? n2 : 0.f;
 }
 
+// Rigorous upper bounds of the powers of (1 + u) and 1 / (1 - u) that the
+// margins need (n u < 1): (1 + u)^m <= (1 - u)^-m <= 1 / (1 - m u) for
+// m <= n, without a call to pow (whose latency on the FP64 unit would
+// serialise the threads that wait for the margin).
+__device__ __forceinline__ double pow_bound(double u, double n) { return 1.0 / (1.0 - ceil(n) * u); }
+
 // Y: all rows (Npad of them), Ys: rows 0, s, 2s, ... (nsamp_pad of them;
 // null when s = 1, where the sample is the whole design).
 __global__ void knn_prep(const void *__restrict__ X, int64_t N, int p, lagp_dtype dt,
                          const unsigned long long *kmax, const unsigned long long *kmin,
                          float *__restrict__ Y, int64_t Npad, float *__restrict__ Ys,
-                         int64_t nsamp_pad, int64_t sstride) {
+                         int64_t nsamp_pad, int64_t sstride, KnnConst *kc) {
     __shared__ double c[64];
     __shared__ double sB;
-    if (threadIdx.x == 0) centre_and_bound(kmax, kmin, p, c, sB);
+    if (threadIdx.x == 0) {
+        centre_and_bound(kmax, kmin, p, c, sB);
+        if (blockIdx.x == 0) {
+            const double u = 0x1p-24 * (1.0 + 0x1p-27);
+            for (int i = 0; i < p; i++) kc->c[i] = c[i];
+            kc->B = sB;
+            kc->e2 = 2.0 * u * sB * sqrt((double)p);
+            kc->g_half = pow_bound(u, 0.5 * (p + 4));
+            kc->g_full = pow_bound(u, (double)(p + 4));
+        }
+    }
     __syncthreads();
     const int ps = row_stride(p);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -177,13 +207,16 @@ __global__ void knn_prep(const void *__restrict__ X, int64_t N, int p, lagp_dtyp
 // The final factors cover the rounding of the FP64 reference distances (the
 // order is that of the FP64 sums, within a relative 1e-15 of r^2) and of
 // this computation.
+// g >= (1 - u)^-(p+4)/2 and (1 + u)^(p+4)/2, e2 = 2uB sqrt(p)
+__device__ __forceinline__ double screen_margin_c(float tau, double g, double e2) {
+    const double r_hi = sqrt((double)tau) * g * (1.0 + 1e-13) + e2;
+    const double r_col = (r_hi + e2) * g;
+    return r_col * r_col * (1.0 + 1e-12);
+}
+
 __device__ double screen_margin(float tau, int p, double B) {
     const double u = 0x1p-24 * (1.0 + 0x1p-27);
-    double e2 = 2.0 * u * B * sqrt((double)p);
-    double r = sqrt((double)tau);
-    double r_hi = r * pow(1.0 - u, -0.5 * (p + 4)) * (1.0 + 1e-13) + e2;
-    double r_col = (r_hi + e2) * pow(1.0 + u, 0.5 * (p + 4));
-    return r_col * r_col * (1.0 + 1e-12);
+    return screen_margin_c(tau, pow_bound(u, 0.5 * (p + 4)), 2.0 * u * B * sqrt((double)p));
 }
 
 __device__ double expansion_margin(float tau, int p, double B) {
@@ -522,11 +555,10 @@ __device__ int block_excl_scan(int v, int *wsum, int *total) {
 // widened by 1e-6 relative, plus 2e-15 Rm^2 for the rounding of the FP64
 // sums that define the order.  Two rows whose FP32 values differ by more
 // than 2 Delta are in the same order by their FP64 distances, strictly.
-__device__ double tie_bound(float tau, int p, double B) {
-    const double u = 0x1p-24 * (1.0 + 0x1p-27);
-    const double e2 = 2.0 * u * B * sqrt((double)p);
-    const double Rm = sqrt((double)tau) * pow(1.0 - u, -0.5 * (p + 4)) * (1.0 + 1e-13) + e2;
-    const double d0 = (pow(1.0 + u, (double)(p + 4)) - 1.0) * (Rm + e2) * (Rm + e2) + 2.0 * Rm * e2 + e2 * e2;
+// g_half >= (1 - u)^-(p+4)/2, g_full >= (1 + u)^(p+4), e2 = 2uB sqrt(p)
+__device__ __forceinline__ double tie_bound(float tau, double g_half, double g_full, double e2) {
+    const double Rm = sqrt((double)tau) * g_half * (1.0 + 1e-13) + e2;
+    const double d0 = (g_full - 1.0) * (Rm + e2) * (Rm + e2) + 2.0 * Rm * e2 + e2 * e2;
     return d0 * (1.0 + 1e-6) + 2e-15 * Rm * Rm;
 }
 
@@ -547,13 +579,79 @@ __device__ __forceinline__ bool pair_less(double da, uint32_t ra, double db, uin
 //      within the run; outside the runs the FP32 order is the FP64 order.
 //      A run longer than 32 sends the query to a full FP64 sort instead;
 //  (6) the first N' rows.
+// Ascending bitonic sort of sk[0, S) (S <= 1,024; the keys past S act as
+// +infinity) by 256 threads, four keys a thread in registers: element e =
+// 128 warp + 4 lane + r.  Compare-exchanges at distance 1, 2 stay in the
+// thread, 4..64 go through warp shuffles, 128..512 through shared memory
+// (two alternating buffers of 1,024 keys, sk and alt: one barrier a step).
+// The sorted keys end in sk[0, 1024).
+__device__ void sort1024_registers(unsigned long long *sk, int S, unsigned long long *alt) {
+    static_assert(SORT_THREADS == 256, "four keys a thread for 1,024");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int base = warp * 128 + lane * 4;
+    unsigned long long x[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) x[r] = base + r < S ? sk[base + r] : ~0ull;
+    __syncthreads();  // every key is read before sk serves as an exchange buffer
+    int buf = 0;
+    for (int size = 2; size <= 1024; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 128) {
+                unsigned long long *b = buf ? alt : sk;
+                buf ^= 1;
+#pragma unroll
+                for (int r = 0; r < 4; r++) b[base + r] = x[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int e = base + r;
+                    const unsigned long long y = b[e ^ stride];
+                    const bool lo = (e & stride) == 0, asc = (e & size) == 0;
+                    x[r] = (lo == asc) ? (y < x[r] ? y : x[r]) : (y > x[r] ? y : x[r]);
+                }
+            } else if (stride >= 4) {
+                const int lm = stride >> 2;
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int e = base + r;
+                    const unsigned long long y = __shfl_xor_sync(LAGP_FULL_MASK, x[r], lm);
+                    const bool lo = (lane & lm) == 0, asc = (e & size) == 0;
+                    x[r] = (lo == asc) ? (y < x[r] ? y : x[r]) : (y > x[r] ? y : x[r]);
+                }
+            } else {
+                // within the thread: pairs (0, 2), (1, 3) at distance 2, (0, 1),
+                // (2, 3) at distance 1 (constant register indices)
+                auto cx = [&](unsigned long long &a, unsigned long long &c, int e) {
+                    const bool asc = (e & size) == 0;
+                    if (asc ? c < a : a < c) {
+                        const unsigned long long t = a;
+                        a = c;
+                        c = t;
+                    }
+                };
+                if (stride == 2) {
+                    cx(x[0], x[2], base);
+                    cx(x[1], x[3], base + 1);
+                } else {
+                    cx(x[0], x[1], base);
+                    cx(x[2], x[3], base + 2);
+                }
+            }
+        }
+    }
+    __syncthreads();  // the last exchange buffer is read before sk is written
+#pragma unroll
+    for (int r = 0; r < 4; r++) sk[base + r] = x[r];
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(SORT_THREADS)
 knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_dtype dt,
          const void *__restrict__ Xref, int64_t M, const int32_t *__restrict__ Np, int32_t Npmax,
          const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
          const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_count, int32_t Cmax,
-         int32_t *__restrict__ idx, const float *__restrict__ tau2v, int32_t *__restrict__ retry,
-         int only_retried) {
+         int32_t *__restrict__ idx, const KnnConst *__restrict__ kc, const float *__restrict__ rcol,
+         int32_t *__restrict__ retry, int only_retried) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t q = blockIdx.x;
     // only_retried: the queries that the exact retry recollected; otherwise
@@ -574,9 +672,9 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     int32_t *rowA = reinterpret_cast<int32_t *>(key32 + Cp);            // Cmax
     double *dk = reinterpret_cast<double *>(smem_raw);                  // Cp
     unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)Cp * 8);  // Cp
-    __shared__ double xq[64], c[64];
+    __shared__ double xq[64];
     __shared__ float yq[64];
-    __shared__ double sB, s_delta2;
+    __shared__ float s_d2f;
     __shared__ uint32_t hist[256];
     __shared__ int wsum[SORT_THREADS / 32];
     __shared__ uint32_t s_prefix;
@@ -584,18 +682,19 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     __shared__ float s_tauf;
     __shared__ uint32_t tied[CAND_CAP / 32];
     const int ps = row_stride(p);
+    if (threadIdx.x < p) {
+        xq[threadIdx.x] = load_coord64(Xref, q, p, threadIdx.x, dt);
+        yq[threadIdx.x] = (float)(xq[threadIdx.x] - kc->c[threadIdx.x]);
+    }
     if (threadIdx.x == 0) {
-        centre_and_bound(kmax, kmin, p, c, sB);
-        for (int i = 0; i < p; i++) {
-            xq[i] = load_coord64(Xref, q, p, i, dt);
-            yq[i] = (float)(xq[i] - c[i]);
-        }
         s_prefix = 0u;
         s_kk = k;
         s_big = 0;
     }
     __syncthreads();
-    // (1) direct-form FP32 values (non-negative floats order like their bits)
+    // (1) direct-form FP32 values (non-negative floats order like their
+    // bits); four rows a thread in flight
+#pragma unroll 4
     for (int e = threadIdx.x; e < C; e += SORT_THREADS) {
         const int32_t r = cand[q * Cmax + e];
         const float *yr = Y32 + (int64_t)r * ps;
@@ -613,9 +712,16 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
         __syncthreads();
         const uint32_t prefix = s_prefix;
         const uint32_t hmask = shift == 24 ? 0u : (0xffffffffu << (shift + 8));
-        for (int e = threadIdx.x; e < C; e += SORT_THREADS) {
-            const uint32_t kv = key32[e];
-            if ((kv & hmask) == prefix) atomicAdd(&hist[(kv >> shift) & 255u], 1u);
+        // one atomic per distinct bin of a warp (most keys share their top bits)
+        const int lane = threadIdx.x & 31;
+        for (int e0 = threadIdx.x - lane; e0 < C; e0 += SORT_THREADS) {
+            uint32_t bin = 0xFFFFFFFFu;
+            if (e0 + lane < C) {
+                const uint32_t kv = key32[e0 + lane];
+                if ((kv & hmask) == prefix) bin = (kv >> shift) & 255u;
+            }
+            const unsigned peers = __match_any_sync(LAGP_FULL_MASK, bin);
+            if (bin != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
         }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -645,20 +751,17 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const float tauf = __double2float_rd(screen_margin(__uint_as_float(s_prefix), p, sB));
+        // the margins with the launch's constants
+        const double g = kc->g_half, e2 = kc->e2;
+        const float vk = __uint_as_float(s_prefix);
+        const double rk = sqrt((double)vk) * g * (1.0 + 1e-13) + e2;  // >= exact N'-th distance
+        const float tauf = __double2float_rd(screen_margin_c(vk, g, e2));
         s_tauf = tauf;
-        s_delta2 = 2.0 * tie_bound(tauf, p, sB);
-        s_fail = 0;
-        if (tau2v) {
-            // rows collected on the tensor cores under tau2: the N'-th of them
-            // (its direct FP32 value s_prefix bounds its exact distance) must
-            // lie within the radius that tau2 guarantees collected, else the
-            // query goes to the exact retry
-            const double u = 0x1p-24 * (1.0 + 0x1p-27);
-            const double e2 = 2.0 * u * sB * sqrt((double)p);
-            const double rk = sqrt((double)__uint_as_float(s_prefix)) * pow(1.0 - u, -0.5 * (p + 4)) * (1.0 + 1e-13) + e2;
-            s_fail = !(rk <= tc_collected_radius(tau2v[q], p, tc_k(p), sB));
-        }
+        s_d2f = __double2float_ru(2.0 * tie_bound(tauf, g, kc->g_full, e2));
+        // rows collected on the tensor cores: the N'-th of them must lie
+        // within the radius collected in full, else the query goes to the
+        // exact retry
+        s_fail = rcol ? !(rk <= (double)rcol[q]) : 0;
     }
     __syncthreads();
     if (s_fail) {
@@ -679,27 +782,33 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     while (Sp < S) Sp <<= 1;
     for (int e = S + threadIdx.x; e < Sp; e += SORT_THREADS) sk[e] = ~0ull;
     __syncthreads();
-    // (4) bitonic sort on (s, row)
-    for (int size = 2; size <= Sp; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int e = threadIdx.x; e < (Sp >> 1); e += SORT_THREADS) {
-                const int lo = 2 * e - (e & (stride - 1)), hi = lo + stride;
-                const bool up = ((lo & size) == 0);
-                const unsigned long long ka = sk[lo], kb = sk[hi];
-                if (up ? kb < ka : ka < kb) {
-                    sk[lo] = kb;
-                    sk[hi] = ka;
+    // (4) bitonic sort on (s, row): up to 1,024 keys in registers (four a
+    // thread), else in shared memory
+    if (Sp <= 4 * SORT_THREADS) {
+        sort1024_registers(sk, S, reinterpret_cast<unsigned long long *>(smem_raw));
+    } else {
+        for (int size = 2; size <= Sp; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int e = threadIdx.x; e < (Sp >> 1); e += SORT_THREADS) {
+                    const int lo = 2 * e - (e & (stride - 1)), hi = lo + stride;
+                    const bool up = ((lo & size) == 0);
+                    const unsigned long long ka = sk[lo], kb = sk[hi];
+                    if (up ? kb < ka : ka < kb) {
+                        sk[lo] = kb;
+                        sk[hi] = ka;
+                    }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     // (5) runs of near-equal FP32 values: FP64 keys, ordered within the run
-    const double d2lim = s_delta2;
+    const float d2f = s_d2f;  // twice the tie bound, rounded up
     auto gap_ok = [&](int i) {  // rows i and i + 1 are in a certain FP64 order
-        const double a = (double)__uint_as_float((uint32_t)(sk[i] >> 32));
-        const double b = (double)__uint_as_float((uint32_t)(sk[i + 1] >> 32));
-        return b - a > d2lim;
+        // the FP32 difference rounded down never exceeds the true one
+        const float a = __uint_as_float((uint32_t)(sk[i] >> 32));
+        const float b = __uint_as_float((uint32_t)(sk[i + 1] >> 32));
+        return __fsub_rd(b, a) > d2f;
     };
     auto fp64_key = [&](int i) {
         const int32_t r = (int32_t)(uint32_t)sk[i];
@@ -801,10 +910,6 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     cudaStream_t st = ctx->stream;
     ctx->knn_last_M = M;
     const int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
-    // meta: the tensor-core screen's failure word (offset 0), two block
-    // counters (offset 64), the coordinate bounds (offsets 256 and 768, 64
-    // keys each), then per-query candidate counts and retry flags
-    constexpr size_t META_HEAD = 1280;
     char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
     int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
     // sample stride: about 8 N' sampled rows per candidate set, 1 (exact) for small designs
@@ -823,17 +928,18 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     LAGP_CUDA(ctx, cudaMemsetAsync(meta, 0, META_HEAD, st));
     const int blocks = ctx->num_sms * 4;
     knn_bounds<<<blocks, 256, 0, st>>>(X, N, Xref, M, p, dtype, kmax, kmin);
+    KnnConst *kc = reinterpret_cast<KnnConst *>(meta + META_CONST);
     knn_prep<<<blocks, 256, 0, st>>>(X, N, p, dtype, kmax, kmin, Y32, Npad, stride > 1 ? Ys : nullptr,
-                                     nsamp_pad, stride);
+                                     nsamp_pad, stride, kc);
     ctx->launches += 2;
     LAGP_CUDA(ctx, cudaGetLastError());
     // collection on the tensor cores unless the tuning asks for CUDA cores
     void *tc_ws = nullptr;
-    float *tau0 = nullptr, *tau2 = nullptr;
+    float *tau0 = nullptr, *rcol = nullptr;
     if (ctx->tuning.knn_path == 0 && knn_tc_supported(p)) {
         tc_ws = lagp_ws(ctx, WS_KNN_TC, knn_tc_workspace(N, M, p));
         if (!tc_ws) return LAGP_ENOMEM;
-        LAGP_TRY(launch_knn_tc_prep(ctx, tc_ws, X, N, p, dtype, Xref, M, kmax, kmin, &tau0, &tau2));
+        LAGP_TRY(launch_knn_tc_prep(ctx, tc_ws, X, N, p, dtype, Xref, M, kmax, kmin, &tau0, &rcol));
     }
     int *tc_err = reinterpret_cast<int *>(meta);
 
@@ -854,9 +960,9 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
             default: launch_screen<0>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
         }
     };
-    auto sort = [&](const float *tau2v, int32_t *rflags, int only_retried) {
+    auto sort = [&](const float *rc, int32_t *rflags, int only_retried) {
         knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Y32, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
-                                                               cand, cc, Cmax, idx, tau2v, rflags, only_retried);
+                                                               cand, cc, Cmax, idx, kc, rc, rflags, only_retried);
         ctx->launches++;
     };
     screen(false);
@@ -865,8 +971,8 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
         // collection on the tensor cores, the sort (which checks each query's
         // collection), the exact retry of the flagged queries and their sort
         LAGP_TRY(launch_knn_tc_collect(ctx, tc_ws, N, p, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, retry,
-                                       tc_err, tau2, nullptr));
-        sort(tau2, retry, 0);
+                                       tc_err, rcol, nullptr));
+        sort(rcol, retry, 0);
         screen(true);
         sort(nullptr, retry, 1);
     } else {
@@ -883,7 +989,6 @@ lagp_status launch_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int p, l
                                const void *Xref, int64_t M, float *out) {
     if (!knn_tc_supported(p)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn_tc_dist: p > 20");
     cudaStream_t st = ctx->stream;
-    constexpr size_t META_HEAD = 1280;
     char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
     void *tc_ws = lagp_ws(ctx, WS_KNN_TC, knn_tc_workspace(N, M, p));
     if (!meta || !tc_ws) return LAGP_ENOMEM;
@@ -895,10 +1000,10 @@ lagp_status launch_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int p, l
     knn_bounds<<<ctx->num_sms * 4, 256, 0, st>>>(X, N, Xref, M, p, dtype, kmax, kmin);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
-    float *tau0 = nullptr, *tau2 = nullptr;
-    LAGP_TRY(launch_knn_tc_prep(ctx, tc_ws, X, N, p, dtype, Xref, M, kmax, kmin, &tau0, &tau2));
+    float *tau0 = nullptr, *rcol = nullptr;
+    LAGP_TRY(launch_knn_tc_prep(ctx, tc_ws, X, N, p, dtype, Xref, M, kmax, kmin, &tau0, &rcol));
     return launch_knn_tc_collect(ctx, tc_ws, N, p, M, nullptr, 1, kmax, kmin, nullptr, 1, cc, nullptr, retry,
-                                 reinterpret_cast<int *>(meta), tau2, out);
+                                 reinterpret_cast<int *>(meta), rcol, out);
 }
 
 // Diagnostic: of the last kNN call on the context, the queries that went to
@@ -911,7 +1016,6 @@ lagp_status knn_last_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed) 
         *tc_failed = 0;
         return LAGP_OK;
     }
-    constexpr size_t META_HEAD = 1280;
     std::vector<int32_t> r((size_t)M);
     int32_t f = 0;
     LAGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

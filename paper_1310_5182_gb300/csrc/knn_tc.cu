@@ -20,7 +20,8 @@
 // (tc_margin) of the sampled threshold tau0 (itself widened by 2 E_tc so that
 // rows at the sample's boundary fall inside whatever the rounding of either
 // pass).  The sort then checks that the N'-th collected row lies within the
-// radius that tau2 guarantees collected (tc_collected_radius); a query that
+// radius that tau2 guarantees collected (tc_collected_radius, stored per
+// query); a query that
 // fails, or whose buffer overflows, goes to the exact CUDA-core retry.  E_tc
 // (knn_common.cuh) assumes that one tensor-core instruction adds its products
 // and accumulator with an error of at most TC_ACC_ULPS = 64 units of 2^-24
@@ -150,7 +151,7 @@ struct TcArgs {
     int64_t N, M;
     int p, K, nmb;
     const float *tau0;  // per query: sampled threshold, NaN = not screened
-    float *tau2;        // per query out: the collection threshold (NaN: not collected)
+    float *rcol;        // per query out: the radius collected in full (rounded down; NaN: not collected)
     const int32_t *Np;
     int32_t Npmax;
     const unsigned long long *kmax, *kmin;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
             const bool done = !failed && ok && s_cnt[c] >= k && s_cnt[c] <= a.Cmax;
             a.retry[q] = (kvalid && !done) ? 1 : 0;
             a.cand_count[q] = done ? s_cnt[c] : 0;
-            a.tau2[q] = done ? s_tau2[c] / s2 : CUDART_NAN_F;
+            a.rcol[q] = done ? __double2float_rd(tc_collected_radius(s_tau2[c] / s2, a.p, K, s_B)) : CUDART_NAN_F;
             if (a.status) a.status[q] = kvalid ? LAGP_OK : LAGP_EINVAL;
         }
         it0 += a.nmb;
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
                     const bool kvalid = k >= 1 && k <= a.Npmax;
                     a.retry[q] = kvalid ? 1 : 0;
                     a.cand_count[q] = 0;
-                    a.tau2[q] = CUDART_NAN_F;
+                    a.rcol[q] = CUDART_NAN_F;
                     if (a.status) a.status[q] = kvalid ? LAGP_OK : LAGP_EINVAL;
                 }
             break;
@@ -419,13 +420,13 @@ size_t knn_tc_workspace(int64_t N, int64_t M, int p) {
 // collection pass.  ws: knn_tc_workspace(N, M, p) bytes.
 lagp_status launch_knn_tc_prep(lagp_ctx *ctx, void *ws, const void *X, int64_t N, int p, lagp_dtype dtype,
                                const void *Xref, int64_t M, const unsigned long long *kmax,
-                               const unsigned long long *kmin, float **tau0, float **tau2) {
+                               const unsigned long long *kmin, float **tau0, float **rcol) {
     const int K = tc_k(p);
     const int64_t Npad = round_up(std::max<int64_t>(N, 1), TC_MROWS);
     __half *A = static_cast<__half *>(ws);
     __half *Q = A + Npad * K;
     *tau0 = reinterpret_cast<float *>(Q + M * K);
-    *tau2 = *tau0 + M;
+    *rcol = *tau0 + M;
     knn_tc_prep<<<ctx->num_sms * 4, 128, 0, ctx->stream>>>(X, N, Npad, Xref, M, p, dtype, kmax, kmin, A, Q);
     ctx->launches++;
     return lagp_cuda_check(ctx, cudaGetLastError(), "knn_tc_prep");
@@ -434,7 +435,7 @@ lagp_status launch_knn_tc_prep(lagp_ctx *ctx, void *ws, const void *X, int64_t N
 lagp_status launch_knn_tc_collect(lagp_ctx *ctx, void *ws, int64_t N, int p, int64_t M, const int32_t *Np,
                                   int32_t Npmax, const unsigned long long *kmax, const unsigned long long *kmin,
                                   int32_t *cand, int32_t Cmax, int32_t *cand_count, int32_t *status,
-                                  int32_t *retry, int *err, float *tau2, float *dump) {
+                                  int32_t *retry, int *err, float *rcol, float *dump) {
     const int K = tc_k(p);
     const int64_t Npad = round_up(std::max<int64_t>(N, 1), TC_MROWS);
     TcArgs a;
@@ -446,7 +447,7 @@ lagp_status launch_knn_tc_collect(lagp_ctx *ctx, void *ws, int64_t N, int p, int
     a.K = K;
     a.nmb = (int)(Npad / TC_MROWS);
     a.tau0 = reinterpret_cast<const float *>(a.Q + M * K);
-    a.tau2 = tau2;
+    a.rcol = rcol;
     a.Np = Np;
     a.Npmax = Npmax;
     a.kmax = kmax;

@@ -77,11 +77,11 @@ bool knn_tc_supported(int p);
 size_t knn_tc_workspace(int64_t N, int64_t M, int p);
 lagp_status launch_knn_tc_prep(lagp_ctx *ctx, void *ws, const void *X, int64_t N, int p, lagp_dtype dtype,
                                const void *Xref, int64_t M, const unsigned long long *kmax,
-                               const unsigned long long *kmin, float **tau0, float **tau2);
+                               const unsigned long long *kmin, float **tau0, float **rcol);
 lagp_status launch_knn_tc_collect(lagp_ctx *ctx, void *ws, int64_t N, int p, int64_t M, const int32_t *Np,
                                   int32_t Npmax, const unsigned long long *kmax, const unsigned long long *kmin,
                                   int32_t *cand, int32_t Cmax, int32_t *cand_count, int32_t *status,
-                                  int32_t *retry, int *err, float *tau2, float *dump);
+                                  int32_t *retry, int *err, float *rcol, float *dump);
 lagp_status launch_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtype dtype,
                                const void *Xref, int64_t M, float *out);
 lagp_status knn_last_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed);
