@@ -157,11 +157,13 @@ __device__ __forceinline__ void centred_row(const void *X, int64_t N, int64_t r,
 __device__ __forceinline__ double pow_bound(double u, double n) { return 1.0 / (1.0 - ceil(n) * u); }
 
 // Y: all rows (Npad of them), Ys: rows 0, s, 2s, ... (nsamp_pad of them;
-// null when s = 1, where the sample is the whole design).
+// null when s = 1, where the sample is the whole design), Yv: the
+// coordinates of Y with a row stride of p rounded up to 4; kc: the launch's
+// constants (block 0).
 __global__ void knn_prep(const void *__restrict__ X, int64_t N, int p, lagp_dtype dt,
                          const unsigned long long *kmax, const unsigned long long *kmin,
                          float *__restrict__ Y, int64_t Npad, float *__restrict__ Ys,
-                         int64_t nsamp_pad, int64_t sstride, KnnConst *kc) {
+                         int64_t nsamp_pad, int64_t sstride, KnnConst *kc, float *__restrict__ Yv) {
     __shared__ double c[64];
     __shared__ double sB;
     if (threadIdx.x == 0) {
@@ -178,8 +180,12 @@ __global__ void knn_prep(const void *__restrict__ X, int64_t N, int p, lagp_dtyp
     __syncthreads();
     const int ps = row_stride(p);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < Npad; r += stride)
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < Npad; r += stride) {
         centred_row(X, N, r, p, ps, dt, c, Y + r * ps);
+        // the same coordinates with a row stride of p rounded up to 4 (vector gathers in the sort)
+        const int pv = (p + 3) & ~3;
+        for (int i = 0; i < pv; i++) Yv[r * pv + i] = i < p ? Y[r * ps + i] : 0.f;
+    }
     if (Ys)
         for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nsamp_pad; r += stride)
             centred_row(X, N, r * sstride, p, ps, dt, c, Ys + r * ps);
@@ -606,8 +612,9 @@ __device__ void sort1024_registers(unsigned long long *sk, int S, unsigned long 
                 for (int r = 0; r < 4; r++) {
                     const int e = base + r;
                     const unsigned long long y = b[e ^ stride];
-                    const bool lo = (e & stride) == 0, asc = (e & size) == 0;
-                    x[r] = (lo == asc) ? (y < x[r] ? y : x[r]) : (y > x[r] ? y : x[r]);
+                    // take y when it belongs here: smaller for the low end of an
+                    // ascending pair (or the high end of a descending one)
+                    if ((y < x[r]) == (((e & stride) == 0) == ((e & size) == 0))) x[r] = y;
                 }
             } else if (stride >= 4) {
                 const int lm = stride >> 2;
@@ -615,8 +622,7 @@ __device__ void sort1024_registers(unsigned long long *sk, int S, unsigned long 
                 for (int r = 0; r < 4; r++) {
                     const int e = base + r;
                     const unsigned long long y = __shfl_xor_sync(LAGP_FULL_MASK, x[r], lm);
-                    const bool lo = (lane & lm) == 0, asc = (e & size) == 0;
-                    x[r] = (lo == asc) ? (y < x[r] ? y : x[r]) : (y > x[r] ? y : x[r]);
+                    if ((y < x[r]) == (((lane & lm) == 0) == ((e & size) == 0))) x[r] = y;
                 }
             } else {
                 // within the thread: pairs (0, 2), (1, 3) at distance 2, (0, 1),
@@ -646,7 +652,7 @@ __device__ void sort1024_registers(unsigned long long *sk, int S, unsigned long 
 }
 
 __global__ void __launch_bounds__(SORT_THREADS)
-knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_dtype dt,
+knn_sort(const void *__restrict__ X, const float *__restrict__ Yv, int p, lagp_dtype dt,
          const void *__restrict__ Xref, int64_t M, const int32_t *__restrict__ Np, int32_t Npmax,
          const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
          const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_count, int32_t Cmax,
@@ -681,7 +687,6 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     __shared__ int s_kk, s_big, s_fail;
     __shared__ float s_tauf;
     __shared__ uint32_t tied[CAND_CAP / 32];
-    const int ps = row_stride(p);
     if (threadIdx.x < p) {
         xq[threadIdx.x] = load_coord64(Xref, q, p, threadIdx.x, dt);
         yq[threadIdx.x] = (float)(xq[threadIdx.x] - kc->c[threadIdx.x]);
@@ -694,14 +699,21 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Y32, int p, lagp_
     __syncthreads();
     // (1) direct-form FP32 values (non-negative floats order like their
     // bits); four rows a thread in flight
+    const int pv = (p + 3) & ~3;  // row stride of Yv
 #pragma unroll 4
     for (int e = threadIdx.x; e < C; e += SORT_THREADS) {
         const int32_t r = cand[q * Cmax + e];
-        const float *yr = Y32 + (int64_t)r * ps;
+        const float4 *yr = reinterpret_cast<const float4 *>(Yv + (int64_t)r * pv);
         float sv = 0.f;
-        for (int i = 0; i < p; i++) {
-            const float df = yr[i] - yq[i];
-            sv = fmaf(df, df, sv);
+        for (int i4 = 0; i4 < pv; i4 += 4) {
+            const float4 v = yr[i4 >> 2];
+            const float t[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (i4 + j < p) {  // coordinate order, as the direct form defines
+                    const float df = t[j] - yq[i4 + j];
+                    sv = fmaf(df, df, sv);
+                }
         }
         key32[e] = __float_as_uint(sv);  // NaN keeps the largest keys
         rowA[e] = r;
@@ -917,9 +929,11 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     const int pp = row_stride(p);
     const int64_t Npad = round_up(N, 32), nsamp = (N + stride - 1) / stride;
     const int64_t nsamp_pad = stride > 1 ? round_up(nsamp, 32) : 0;
-    float *Y32 = static_cast<float *>(lagp_ws(ctx, WS_KNN_X32, (size_t)(Npad + nsamp_pad) * pp * 4));
+    const int pv = (p + 3) & ~3;
+    float *Y32 = static_cast<float *>(lagp_ws(ctx, WS_KNN_X32, ((size_t)(Npad + nsamp_pad) * pp + (size_t)Npad * pv) * 4));
     if (!meta || !cand || !Y32) return LAGP_ENOMEM;
     float *Ys = stride > 1 ? Y32 + Npad * pp : Y32;
+    float *Yv = Y32 + (Npad + nsamp_pad) * pp;  // 16-byte aligned: Npad is a multiple of 32
     int *counters = reinterpret_cast<int *>(meta + 64);
     unsigned long long *kmax = reinterpret_cast<unsigned long long *>(meta + 256);
     unsigned long long *kmin = reinterpret_cast<unsigned long long *>(meta + 768);
@@ -930,7 +944,7 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     knn_bounds<<<blocks, 256, 0, st>>>(X, N, Xref, M, p, dtype, kmax, kmin);
     KnnConst *kc = reinterpret_cast<KnnConst *>(meta + META_CONST);
     knn_prep<<<blocks, 256, 0, st>>>(X, N, p, dtype, kmax, kmin, Y32, Npad, stride > 1 ? Ys : nullptr,
-                                     nsamp_pad, stride, kc);
+                                     nsamp_pad, stride, kc, Yv);
     ctx->launches += 2;
     LAGP_CUDA(ctx, cudaGetLastError());
     // collection on the tensor cores unless the tuning asks for CUDA cores
@@ -961,7 +975,7 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
         }
     };
     auto sort = [&](const float *rc, int32_t *rflags, int only_retried) {
-        knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Y32, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
+        knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Yv, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
                                                                cand, cc, Cmax, idx, kc, rc, rflags, only_retried);
         ctx->launches++;
     };
