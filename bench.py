@@ -90,12 +90,17 @@ def fp32_flops_per_location(n, Np, p):
     return sum((Np - j - 1) * (2 * j + 3 * p + 8) for j in range(0, n - 1))
 
 
+# FP64 flops of one table-driven exp (seven fused multiply-adds, a subtract
+# and a multiply)
+EXP_FLOPS = 16
+
+
 def fp64_schur_pass_flops_per_location(n, Np, p):
     """FP64 flops of the FP64 Schur form's bulk pass: after step j every
     unchosen candidate takes the dot product with the pivot column (2j), its
-    squared distance to the new point (3p), the scale by -1/d and the 20
-    flops of the table-driven exp, and the updates of u, v and r (6)."""
-    return sum((Np - j - 1) * (2 * j + 3 * p + 27) for j in range(0, n - 1))
+    squared distance to the new point (3p), the scale by -1/d and the
+    EXP_FLOPS of the table-driven exp, and the updates of u, v and r (6)."""
+    return sum((Np - j - 1) * (2 * j + 3 * p + 7 + EXP_FLOPS) for j in range(0, n - 1))
 
 
 def fp64_flops(work, M, n, p, fused):
@@ -103,13 +108,13 @@ def fp64_flops(work, M, n, p, fused):
     (sums over steps of the contenders re-scored, n_c, of n_c j and n_c j^2).
     Per contender at design size j: its j + 1 kernel values (p subtracts and
     p fused multiply-adds for the squared distance, the scale by -1/d, and the
-    20 flops of the table-driven exp), the contraction with [K^{-1} | a (|
+    EXP_FLOPS of the table-driven exp), the contraction with [K^{-1} | a (|
     alpha)] (2 j (j + e), e = 2 with the fused prediction, else 1), k^T b (2j)
     and 12 flops of scalars (Eqs. piedef, dxy).  Per step: mu b (j), the
     symmetric rank-one update of K^{-1} (j (j + 1)), the updates of a (and
     alpha) (2 j e) and 10 flops of scalars."""
     e = 2 if fused else 1
-    cf = 3 * p + 21
+    cf = 3 * p + 1 + EXP_FLOPS
     per_con = work["rescored"] * (cf + 12) + work["rescored_j"] * (cf + 2 * e + 2) + 2 * work["rescored_j2"]
     per_step = M * sum(j * j + (2 + 2 * e) * j + 10 for j in range(n))
     return per_con + per_step
@@ -118,8 +123,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "61d26eb2fbdec306ed052aa6f660316fd98678f676890e49fc189fb2b7a4e116",
-               "dram_bytes_per_location": (4.193914e9 + 0.673965e9) / 3040}
+ALC_TRAFFIC = {"sha256": "29ebf33f744a399e04f4913b4d339e69c04529876f36ca9237e81b8ddd728133",
+               "dram_bytes_per_location": (4.041566e9 + 0.683295e9) / 3040}
 
 
 def alc_source_hash():
@@ -285,7 +290,7 @@ def alc_eval_sweep(L, dev, flush, ns=range(16, 513, 4), Nc=60_000, oracle_ns=(16
     The factorisation of K_n (one CTA) is timed apart from the
     candidates' evaluation, as the paper times the ALC computation with the
     matrices given.  FP64 flops per candidate: n^2 (the triangular solve) +
-    n (3p + 21) (kernel values) + 4n (s, q) + 10."""
+    n (3p + 1 + EXP_FLOPS) (kernel values) + 4n (s, q) + 10."""
     import torch
     w = W.toy2d(seed=0, N=100_000, M=1)
     d2 = ((w.X - w.Xref[0]) ** 2).sum(1)
@@ -315,7 +320,7 @@ def alc_eval_sweep(L, dev, flush, ns=range(16, 513, 4), Nc=60_000, oracle_ns=(16
         ms = statistics.median(ts)
         rows.append((n, ms, statistics.median(tp)))
     p = w.p
-    flops = lambda n: Nc * (n * n + n * (3 * p + 21) + 4 * n + 10)
+    flops = lambda n: Nc * (n * n + n * (3 * p + 1 + EXP_FLOPS) + 4 * n + 10)
     out = {"workload": "toy2d_N100000_one_location_Nprime60000", "Nprime": Nc,
            "n": [r[0] for r in rows], "eval_ms": [r[1] for r in rows], "prep_ms": [r[2] for r in rows],
            "cand_evals_per_sec": [Nc / (r[1] / 1e3) for r in rows],

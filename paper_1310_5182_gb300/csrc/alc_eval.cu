@@ -35,9 +35,9 @@ eval_prep_kernel(const void *X, int p, lagp_dtype dt, const double *x, const int
     double *xd = reinterpret_cast<double *>(smem_raw);  // n x p design coordinates
     double *kx = xd + (size_t)n * p;                    // np
     __shared__ int s_ok;
-    __shared__ double etab[64];
+    __shared__ double etab[EXP64_TABLE_SIZE];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 64) etab[tid] = exp64_table_g[tid];
+    for (int i = tid; i < EXP64_TABLE_SIZE; i += PREP_THREADS) etab[i] = exp64_table_g[i];
     if (tid == 0) s_ok = 1;
     for (int e = tid; e < n * p; e += PREP_THREADS) xd[e] = load_coord64(X, design[e / p], p, e % p, dt);
     __syncthreads();
@@ -116,11 +116,11 @@ eval_cands_kernel(const void *X, int p, lagp_dtype dt, const double *x, const in
     double *blk = reinterpret_cast<double *>(smem_raw);  // EV_B x EV_B block of L
     double *xd = blk + EV_B * EV_B;                       // n x p design coordinates
     double *xc = xd + (size_t)n * p;                      // EV_THREADS x p candidate coordinates
-    __shared__ double etab[64];
+    __shared__ double etab[EXP64_TABLE_SIZE];
     const int tid = threadIdx.x;
     const int64_t c = (int64_t)blockIdx.x * EV_THREADS + tid;
     const bool live = c < Nc;
-    if (tid < 64) etab[tid] = exp64_table_g[tid];
+    for (int i = tid; i < EXP64_TABLE_SIZE; i += EV_THREADS) etab[i] = exp64_table_g[i];
     for (int e = tid; e < n * p; e += EV_THREADS) xd[e] = load_coord64(X, design[e / p], p, e % p, dt);
     const int32_t crow = live ? cands[c] : 0;
     for (int i = 0; i < p; i++) xc[(size_t)tid * p + i] = load_coord64(X, crow, p, i, dt);

@@ -222,8 +222,8 @@ alc_bulk_kernel(F32Params P) {
     double *kx = Kinv + (size_t)(nmax + 1) * ld;                // nmax (even): k_j(x)
     double *xd = kx + ((nmax + 1) & ~1);                        // nmax x p: design coordinates
     double *xq = xd + (size_t)nmax * p;                         // p (even): reference location
-    double *etab = xq + ((p + 1) & ~1);                         // 64: table of exp64_tang
-    double *con_k = etab + 64;                                  // tmax x ld: k_j(x_c), FP64
+    double *etab = xq + ((p + 1) & ~1);                         // EXP64_TABLE_SIZE: table of exp64_tang
+    double *con_k = etab + EXP64_TABLE_SIZE;                                  // tmax x ld: k_j(x_c), FP64
     double *con_b = con_k + (size_t)tmax * ld;                  // tmax x ld: K^{-1} k_j(x_c)
     double *cpart = con_b + (size_t)tmax * ld;                  // max(8,tmax) x ld partials;
                                                                 // row 0 then holds mu b of the winner
@@ -260,7 +260,7 @@ alc_bulk_kernel(F32Params P) {
     // (warp w runs on sub-partition w mod 4)
     const int rot = (blockIdx.x / P.num_sms) & 3;
     const int lead = 32 * rot;  // the thread with the CTA's scalar duties
-    if (tid < 64) etab[tid] = exp64_table_g[tid];
+    for (int i = tid; i < EXP64_TABLE_SIZE; i += F32_THREADS) etab[i] = exp64_table_g[i];
     if (tid < 4) s_work[tid] = 0ull;
 
     for (;;) {
@@ -767,7 +767,7 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     const size_t ld = (nmax + 3) & ~(size_t)1;
     const size_t union_doubles = std::max((size_t)Npad, (2 * (size_t)tmax + std::max(F32_WARPS, tmax)) * ld);
     const size_t smem = 8 * ((nmax + 1) * ld + ((nmax + 1) & ~(size_t)1) + nmax * p + ((p + 1) & ~(size_t)1) +
-                             64 + union_doubles) +
+                             EXP64_TABLE_SIZE + union_doubles) +
                         sizeof(T) * (ld + p);
     if (smem > ctx->smem_optin)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, p too large)");

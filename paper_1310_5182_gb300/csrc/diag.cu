@@ -9,8 +9,8 @@
 namespace {
 
 __global__ void exp64_check_kernel(const double *a, int64_t n, double *out_tang, double *out_lib) {
-    __shared__ double tab[64];
-    if (threadIdx.x < 64) tab[threadIdx.x] = exp64_table_g[threadIdx.x];
+    __shared__ double tab[EXP64_TABLE_SIZE];
+    for (int i = threadIdx.x; i < EXP64_TABLE_SIZE; i += blockDim.x) tab[i] = exp64_table_g[i];
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         out_tang[i] = exp64_tang(a[i], tab);

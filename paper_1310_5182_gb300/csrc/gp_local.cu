@@ -332,7 +332,7 @@ __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
     S.dx = S.kx + nmax;
     S.rd = S.dx + nmax;  // 1 / diag of the current Cholesky factor
     S.xq = S.rd + nmax;
-    S.etab = S.xq + p;  // 64: table of exp64_tang
+    S.etab = S.xq + p;  // EXP64_TABLE_SIZE: table of exp64_tang
     return S;
 }
 
@@ -350,7 +350,7 @@ predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
-    for (int i = threadIdx.x; i < 64; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
+    for (int i = threadIdx.x; i < EXP64_TABLE_SIZE; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     __shared__ double red[GP_WARPS];
@@ -413,7 +413,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
-    for (int i = threadIdx.x; i < 64; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
+    for (int i = threadIdx.x; i < EXP64_TABLE_SIZE; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     __shared__ double red[GP_WARPS];
@@ -498,7 +498,7 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
-    for (int i = threadIdx.x; i < 64; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
+    for (int i = threadIdx.x; i < EXP64_TABLE_SIZE; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     __shared__ double red[GP_WARPS];
@@ -604,7 +604,7 @@ struct GpLaunch {
 template <typename Kern>
 lagp_status prepare(lagp_ctx *ctx, const GpArgs &a, Kern kern, GpLaunch &L) {
     const int ld = (a.nmax + 31) & ~31;
-    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p + 64) * 8 + 64;
+    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p + EXP64_TABLE_SIZE) * 8 + 64;
     if (L.smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "n_max x p too large");
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     int occ = 0;

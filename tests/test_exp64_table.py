@@ -26,32 +26,39 @@ def const(name):
     return float.fromhex(m.group(1))
 
 
-def test_table_is_2_pow_k_over_64():
+NT = 1024  # table entries
+
+
+def test_table_is_2_pow_k_over_1024():
+    assert re.search(r"EXP64_TABLE_SIZE\s*=\s*1024;", SRC)
     body = SRC[SRC.index("#define LAGP_EXP64_TABLE"):SRC.index("static __device__")]
     vals = [float.fromhex(h) for h in re.findall(r"0x[0-9a-f.]+p[+-]\d+", body)]
-    assert len(vals) == 64
+    assert len(vals) == NT
     for k, v in enumerate(vals):
-        assert v == nearest(Decimal(2) ** (Decimal(k) / 64)), k
+        assert v == nearest(Decimal(2) ** (Decimal(k) / NT)), k
 
 
 def test_reduction_constants():
-    assert const("EXP64_INV_L") == nearest(64 / LN2)
+    assert const("EXP64_INV_L") == nearest(NT / LN2)
     hi, lo = const("EXP64_L_HI"), const("EXP64_L_LO")
-    L = Fraction(LN2 / 64)
-    # L_HI: at most 36 significant bits, so N * L_HI is exact for |N| < 2^17
+    L = Fraction(LN2 / NT)
+    # L_HI: at most 33 significant bits, so N * L_HI is exact for |N| < 2^20
+    # (|a| <= 700 gives |N| <= 700 * 1024 / ln 2 < 2^20)
     m, e = math.frexp(hi)
-    assert (Fraction(m) * 2 ** 36).denominator == 1
-    assert abs(Fraction(hi) - L) < Fraction(1, 2 ** 36) * Fraction(hi)
+    assert (Fraction(m) * 2 ** 33).denominator == 1
+    assert 700 * NT / math.log(2) < 2 ** 20
+    assert abs(Fraction(hi) - L) < Fraction(1, 2 ** 33) * Fraction(hi)
     assert lo == nearest(L - Fraction(hi))
     assert const("EXP64_SHIFT") == 1.5 * 2.0 ** 52
-    for k in range(2, 7):
+    for k in range(2, 5):
         assert const(f"EXP64_C{k}") == nearest(Fraction(1, math.factorial(k))), k
+    assert "EXP64_C5" not in SRC
     bits = int(re.search(r"EXP64_FAST_MAX_BITS\s*=\s*(0x[0-9a-fA-F]+)LL", SRC).group(1), 16)
     assert struct.unpack("<d", struct.pack("<Q", bits))[0] == 700.0
 
 
 def test_polynomial_degree_suffices():
-    # |r| <= ln2/128 after reduction; the degree-6 Taylor remainder is below
-    # r^7/7! * e^|r|, far under half an ulp of exp(r) ~ 1
-    r = math.log(2) / 128 * (1 + 1e-12)
-    assert r ** 7 / math.factorial(7) * math.exp(r) < 2.0 ** -60
+    # |r| <= ln2/2048 after reduction; the degree-4 Taylor remainder is below
+    # r^5/5! * e^|r|, far under half an ulp of exp(r) ~ 1
+    r = math.log(2) / (2 * NT) * (1 + 1e-12)
+    assert r ** 5 / math.factorial(5) * math.exp(r) < 2.0 ** -60
