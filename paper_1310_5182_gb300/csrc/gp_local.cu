@@ -239,30 +239,75 @@ struct Derivs {
 };
 
 // First and second d-derivatives of l (and dl/dg); needs K, L, a, psi.
-// K' = (D/d^2) o E goes into Li's storage once L^{-1} is no longer needed.
+// The two traces with K' come from one of two products:
+//   L_FREE (L is not needed afterwards): K' in A1's storage, C = L^{-1} K'
+//     into L's storage (n^3/2 FMAs), and B = C L^{-T} = L^{-1} K' L^{-T}
+//     (symmetric) over its lower triangle only (n^3/6), never stored:
+//     tr(K^{-1} K') = tr(B), tr(K^{-1} K' K^{-1} K') = |B|_F^2;
+//   otherwise: K' in Li's storage once K^{-1} is built, A1 = K^{-1} K' (n^3).
+template <bool L_FREE>
 __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const double *a, double psi,
                               const double *rd, double *t1, double *t2, double *red, const Blk &b) {
     inverse_from_L(W, nm, ld, rd, b);
     const double id2 = 1.0 / (d * d), id3 = id2 / d, id4 = id2 * id2;
-    double *Kp = W.Li;
+    double *Kp = L_FREE ? W.A1 : W.Li;
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
         const int i = e / nm, k = e - i * nm;
         const double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
         Kp[(size_t)i * ld + k] = (W.D[(size_t)i * ld + k] * id2) * E;
     }
     __syncthreads();
-    // A1 = K^{-1} K' (two accumulation chains per element)
-    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
-        const int i = e / nm, k = e - i * nm;
-        const double *Kir = W.Ki + (size_t)i * ld;
-        double s0 = 0.0, s1 = 0.0;
-        int r = 0;
-        for (; r + 2 <= nm; r += 2) {
-            s0 = fma(Kir[r], Kp[(size_t)r * ld + k], s0);
-            s1 = fma(Kir[r + 1], Kp[(size_t)(r + 1) * ld + k], s1);
+    double trA1 = 0.0, trA1A1 = 0.0;
+    if constexpr (L_FREE) {
+        // C = L^{-1} K': C[i][k] = sum_{m <= i} Li[i][m] K'[m][k]
+        double *Cm = W.L;
+        for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+            const int i = e / nm, k = e - i * nm;
+            const double *Lir = W.Li + (size_t)i * ld;
+            double s0 = 0.0, s1 = 0.0;
+            int m = 0;
+            for (; m + 2 <= i + 1; m += 2) {
+                s0 = fma(Lir[m], Kp[(size_t)m * ld + k], s0);
+                s1 = fma(Lir[m + 1], Kp[(size_t)(m + 1) * ld + k], s1);
+            }
+            if (m <= i) s0 = fma(Lir[m], Kp[(size_t)m * ld + k], s0);
+            Cm[(size_t)i * ld + k] = s0 + s1;
         }
-        if (r < nm) s0 = fma(Kir[r], Kp[(size_t)r * ld + k], s0);
-        W.A1[(size_t)i * ld + k] = s0 + s1;
+        __syncthreads();
+        // B[i][j] = sum_{k <= j} C[i][k] Li[j][k], lower triangle i >= j
+        for (int e = b.tid; e < nm * (nm + 1) / 2; e += GP_THREADS) {
+            int i, j;
+            tri_index(e, i, j);
+            const double *Cr = Cm + (size_t)i * ld, *Lj = W.Li + (size_t)j * ld;
+            double s0 = 0.0, s1 = 0.0;
+            int k = 0;
+            for (; k + 2 <= j + 1; k += 2) {
+                s0 = fma(Cr[k], Lj[k], s0);
+                s1 = fma(Cr[k + 1], Lj[k + 1], s1);
+            }
+            if (k <= j) s0 = fma(Cr[k], Lj[k], s0);
+            const double Bij = s0 + s1;
+            if (i == j) {
+                trA1 += Bij;
+                trA1A1 = fma(Bij, Bij, trA1A1);
+            } else {
+                trA1A1 = fma(2.0 * Bij, Bij, trA1A1);
+            }
+        }
+    } else {
+        // A1 = K^{-1} K' (two accumulation chains per element)
+        for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
+            const int i = e / nm, k = e - i * nm;
+            const double *Kir = W.Ki + (size_t)i * ld;
+            double s0 = 0.0, s1 = 0.0;
+            int r = 0;
+            for (; r + 2 <= nm; r += 2) {
+                s0 = fma(Kir[r], Kp[(size_t)r * ld + k], s0);
+                s1 = fma(Kir[r + 1], Kp[(size_t)(r + 1) * ld + k], s1);
+            }
+            if (r < nm) s0 = fma(Kir[r], Kp[(size_t)r * ld + k], s0);
+            W.A1[(size_t)i * ld + k] = s0 + s1;
+        }
     }
     // t1 = K' a
     for (int i = b.tid; i < nm; i += GP_THREADS) {
@@ -271,17 +316,17 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
         t1[i] = s;
     }
     __syncthreads();
-    double trA1 = 0.0, trA1A1 = 0.0, trKiK2 = 0.0, aK2a = 0.0, trKi = 0.0, ata = 0.0;
+    double trKiK2 = 0.0, aK2a = 0.0, trKi = 0.0, ata = 0.0;
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
         int i = e / nm, k = e - i * nm;
-        trA1A1 = fma(W.A1[(size_t)i * ld + k], W.A1[(size_t)k * ld + i], trA1A1);
+        if (!L_FREE) trA1A1 = fma(W.A1[(size_t)i * ld + k], W.A1[(size_t)k * ld + i], trA1A1);
         double Dik = W.D[(size_t)i * ld + k];
         double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
         double K2 = (Dik * Dik * id4 - 2.0 * Dik * id3) * E;
         trKiK2 = fma(W.Ki[(size_t)i * ld + k], K2, trKiK2);
         aK2a = fma(a[i] * K2, a[k], aK2a);
         if (i == k) {
-            trA1 += W.A1[(size_t)i * ld + i];
+            if (!L_FREE) trA1 += W.A1[(size_t)i * ld + i];
             trKi += W.Ki[(size_t)i * ld + i];
             ata = fma(a[i], a[i], ata);
         }
@@ -438,7 +483,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
             if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                dr = llik_derivs(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
+                dr = llik_derivs<true>(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
                 while (it < max_iter) {
                     it++;
                     double delta;
@@ -469,7 +514,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     d = dn;
                     l = ln;
                     psi = psin;
-                    dr = llik_derivs(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
+                    dr = llik_derivs<true>(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
                     if (step < 1e-10 * d) break;
                 }
             }
@@ -521,7 +566,7 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
             if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                Derivs dr = llik_derivs(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
+                Derivs dr = llik_derivs<false>(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
                 // kx, kx_d = (Dx/d^2) kx ; b = K^{-1} kx (t1) by the two triangular
                 // solves (w = L^{-1} kx in t3, v = 1 + g - w^T w: no explicit
                 // inverse, no cancellation against k^T b), K'a (t2), K'b (t3)
