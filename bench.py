@@ -123,8 +123,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "29ebf33f744a399e04f4913b4d339e69c04529876f36ca9237e81b8ddd728133",
-               "dram_bytes_per_location": (4.041566e9 + 0.683295e9) / 3040}
+ALC_TRAFFIC = {"sha256": "c03ae095d36b71b13db02194efd8bd41c2404a3d1fcbe6bc7fea8bb6dd8c18e8",
+               "dram_bytes_per_location": (4.22e9 + 0.68691e9) / 3040}
 
 
 def alc_source_hash():

@@ -680,7 +680,7 @@ alc_bulk_kernel(F32Params P) {
                 for (int r = 0; r < CPT; r++) acc[r] = T(0);
                 const T *Ub = U + c0;
                 // loads in flight per thread: UNR rows of CPT values
-                constexpr int UNR = (F64STATE || CPT >= 16) ? 2 : 4;
+                constexpr int UNR = (F64STATE || CPT >= 16) ? 2 : 6;
                 int i = 0;
                 for (; i + UNR <= j; i += UNR) {
                     T u[UNR][CPT];
