@@ -40,6 +40,28 @@ __device__ double block_sum(double v, double *red, const Blk &b) {
     return s;
 }
 
+// Block sums of NV values at once: warp sums, then one warp adds the warps'
+// partials (not every thread); three barriers for all NV.
+template <int NV>
+__device__ void block_sums(double (&v)[NV], const Blk &b) {
+    __shared__ double part[GP_WARPS * NV], tot[NV];
+#pragma unroll
+    for (int i = 0; i < NV; i++) v[i] = warp_sum(v[i]);
+    __syncthreads();  // earlier readers of part / tot are done
+    if (b.lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; i++) part[b.warp * NV + i] = v[i];
+    __syncthreads();
+    if (b.warp == 0 && b.lane < NV) {
+        double t = 0.0;
+        for (int w = 0; w < GP_WARPS; w++) t += part[w * NV + b.lane];
+        tot[b.lane] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; i++) v[i] = tot[i];
+}
+
 // Lower Cholesky of the symmetric n x n matrix A (lower triangle used) into L,
 // left-looking, with rd = 1 / diag(L).  Returns false (block-uniform) if a
 // pivot is not positive.
@@ -54,12 +76,13 @@ __device__ bool block_cholesky(const double *A, double *L, double *rd, int n, in
             if (b.lane == 0) {
                 double piv = A[(size_t)c * ld + c] - s;
                 if (!(piv > 0.0)) *flag = 0;
-                L[(size_t)c * ld + c] = piv > 0.0 ? sqrt(piv) : 1.0;
+                const double lcc = piv > 0.0 ? sqrt(piv) : 1.0;
+                L[(size_t)c * ld + c] = lcc;
+                rd[c] = 1.0 / lcc;  // once, not in every thread (the FP64 unit is the bound)
             }
         }
         __syncthreads();
-        const double rcc = 1.0 / L[(size_t)c * ld + c];
-        if (b.tid == 0) rd[c] = rcc;
+        const double rcc = rd[c];
         for (int i = c + 1 + b.tid; i < n; i += GP_THREADS) {
             double s0 = A[(size_t)i * ld + c], s1 = 0.0;
             int k = 0;
@@ -194,8 +217,15 @@ __device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, dou
     }
     const double logdet = block_sum(ld_part, red, b);
     const double psi = block_sum(psi_part, red, b);
-    const double hn = 0.5 * nm;
-    *out_l = lgamma(hn) - hn * log(2.0 * CUDART_PI) - 0.5 * logdet - hn * log(psi / 2.0);
+    // the constant and the logarithms on one thread (every thread evaluating
+    // lgamma would hold the FP64 unit for nothing), then broadcast
+    __shared__ double s_l;
+    if (b.tid == 0) {
+        const double hn = 0.5 * nm;
+        s_l = lgamma(hn) - hn * log(2.0 * CUDART_PI) - 0.5 * logdet - hn * log(psi / 2.0);
+    }
+    __syncthreads();
+    *out_l = s_l;
     *out_psi = psi;
     return true;
 }
@@ -343,21 +373,26 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
         phi_p = fma(a[i], t1[i], phi_p);
         chi_p = fma(t1[i], t2[i], chi_p);
     }
-    trA1 = block_sum(trA1, red, b);
-    trA1A1 = block_sum(trA1A1, red, b);
-    trKiK2 = block_sum(trKiK2, red, b);
-    aK2a = block_sum(aK2a, red, b);
-    trKi = block_sum(trKi, red, b);
-    ata = block_sum(ata, red, b);
-    const double phi = block_sum(phi_p, red, b);
-    const double chi = block_sum(chi_p, red, b);
-    const double hn = 0.5 * nm;
-    Derivs r;
-    r.dl = -0.5 * trA1 + hn * phi / psi;
-    r.d2l = 0.5 * trA1A1 - 0.5 * trKiK2 + hn * ((aK2a - 2.0 * chi) / psi + phi * phi / (psi * psi));
-    r.dldg = -0.5 * trKi + hn * ata / psi;
-    r.trKi = trKi;
-    return r;
+    double sums[8] = {trA1, trA1A1, trKiK2, aK2a, trKi, ata, phi_p, chi_p};
+    block_sums<8>(sums, b);
+    trA1 = sums[0];
+    trA1A1 = sums[1];
+    trKiK2 = sums[2];
+    aK2a = sums[3];
+    trKi = sums[4];
+    ata = sums[5];
+    const double phi = sums[6], chi = sums[7];
+    // the scalars on one thread (divisions hold the FP64 unit), then broadcast
+    __shared__ Derivs s_r;
+    if (b.tid == 0) {
+        const double hn = 0.5 * nm, ipsi = 1.0 / psi;
+        s_r.dl = -0.5 * trA1 + hn * phi * ipsi;
+        s_r.d2l = 0.5 * trA1A1 - 0.5 * trKiK2 + hn * ((aK2a - 2.0 * chi) * ipsi + phi * phi * (ipsi * ipsi));
+        s_r.dldg = -0.5 * trKi + hn * ata * ipsi;
+        s_r.trKi = trKi;
+    }
+    __syncthreads();
+    return s_r;
 }
 
 struct GpShared {
