@@ -187,6 +187,14 @@ lagp_status lagp_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
  * bounded wait (its locations then went to the retry).  Synchronises. */
 lagp_status lagp_knn_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed);
 
+/* Test hook for failure detection: the next tensor-core pass of lagp_knn on
+ * this context stops feeding its pipeline after the first design block, so
+ * that its bounded waits (2 s each) run out.  The pass then reports the
+ * failure (lagp_knn_stats: tc_failed = 1) and the exact CUDA-core retry
+ * recomputes all its locations: the call's results are unchanged, only
+ * slower.  No GPU fault is involved. */
+lagp_status lagp_knn_tc_stall(lagp_ctx *ctx);
+
 /* ---------------------------------------------- a2..a6: greedy ALC search
  * Local designs by the greedy ALC search of Fig. 1 step 2: the first n0
  * candidates of idx form X_{n0}(x); for j = n0..n[m]-1 the candidate that

@@ -160,6 +160,7 @@ struct TcArgs {
     int nq, nblocks;  // queries per block, blocks
     int stages;       // shared-memory stages of the design ring
     float *dump;      // diagnostic: every value s (M x N) instead of the collection
+    int stall;        // test hook: the producer stops after the first design block
     int *err;         // raised when a bounded wait gave up (the block's queries go to the retry)
 };
 
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
             if (lane == 0) {  // producer: design blocks into the stage ring
                 int issued = 0;
                 for (int mb = 0; mb < a.nmb && !*err; mb++) {
+                    if (a.stall && mb == 1) break;  // the MMA's wait on this block then runs out
                     const long long it = it0 + mb;
                     const int s = (int)(it % S);
                     const uint32_t round = (uint32_t)(it / S);
@@ -459,6 +461,8 @@ lagp_status launch_knn_tc_collect(lagp_ctx *ctx, void *ws, int64_t N, int p, int
     a.retry = retry;
     a.err = err;
     a.dump = dump;
+    a.stall = ctx->knn_tc_stall;
+    ctx->knn_tc_stall = 0;
     // blocks: a multiple of the SM count (balanced waves), at most TC_QMAX queries each
     const int64_t sms = ctx->num_sms;
     const int64_t nb_min = (M + TC_QMAX - 1) / TC_QMAX;

@@ -192,6 +192,12 @@ lagp_status lagp_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
     return launch_knn_tc_dist(ctx, X, N, p, dtype, Xref, M, out);
 }
 
+lagp_status lagp_knn_tc_stall(lagp_ctx *ctx) {
+    if (!ctx) return LAGP_EINVAL;
+    ctx->knn_tc_stall = 1;
+    return LAGP_OK;
+}
+
 lagp_status lagp_knn_stats(lagp_ctx *ctx, int64_t *n_retry, int32_t *tc_failed) {
     if (!ctx || !n_retry || !tc_failed) return LAGP_EINVAL;
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));

@@ -39,6 +39,7 @@ struct lagp_ctx {
     int tune_override = 0;  // set by the autotuner while it times a candidate
     bool work_zeroed = false;  // ALC work counters cleared once after allocation
     int64_t knn_last_M = 0;    // queries of the last lagp_knn call (for lagp_knn_stats)
+    int knn_tc_stall = 0;      // test hook for the next tensor-core kNN pass (lagp_knn_tc_stall)
 };
 
 // Shape key of an ALC launch for the autotuner's table.

@@ -78,12 +78,13 @@ def _load():
     lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
     lib.lagp_knn_tc_dist.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P]
     lib.lagp_knn_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I32)]
+    lib.lagp_knn_tc_stall.argtypes = [P]
     for f in ("lagp_create", "lagp_destroy", "lagp_set_stream", "lagp_get_tuning", "lagp_set_tuning",
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
               "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_alc_eval",
-              "lagp_scale_inputs", "lagp_knn_tc_dist", "lagp_knn_stats"):
+              "lagp_scale_inputs", "lagp_knn_tc_dist", "lagp_knn_stats", "lagp_knn_tc_stall"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -271,6 +272,13 @@ def lagp_knn_tc_dist(X: torch.Tensor, Xref: torch.Tensor) -> torch.Tensor:
     _check(_lib.lagp_knn_tc_dist(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref"), M,
                                  _dev(out, "out")), ctx, "lagp_knn_tc_dist")
     return out
+
+
+def knn_tc_stall(device=None):
+    """Test hook: the next tensor-core kNN pass on this device's context stops
+    feeding its pipeline, so that its bounded waits run out (see lagp.h)."""
+    ctx = context(device)
+    _check(_lib.lagp_knn_tc_stall(ctx), ctx, "lagp_knn_tc_stall")
 
 
 def knn_stats(device=None) -> dict:

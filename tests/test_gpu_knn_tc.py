@@ -116,3 +116,25 @@ def test_tc_and_cuda_core_paths_agree(L, case):
     # the sampled threshold sends the same few locations to the exact retry
     # (the wider tensor-core margin adds at most a few overflows)
     assert stats["retried"] <= stats_cc["retried"] + max(1, len(Xr) // 100), (stats, stats_cc)
+
+
+def test_bounded_wait_reports_and_retries(L):
+    """Failure detection without a GPU fault: the test hook stops the
+    pass's producer after the first design block, the MMA thread's bounded
+    wait on the next block runs out (2 s), the pass reports it, and the exact
+    retry recomputes every location: the neighbour sets are unchanged."""
+    rng = np.random.default_rng(41)
+    X = rng.uniform(0, 1, (5_000, 8))
+    Xr = rng.uniform(0, 1, (40, 8))
+    ref, st_ref = L.lagp_knn(dev(X), dev(Xr), 200)
+    assert L.knn_stats()["tc_failed"] == 0
+    L.knn_tc_stall()
+    idx, st = L.lagp_knn(dev(X), dev(Xr), 200)
+    stats = L.knn_stats()
+    assert stats["tc_failed"] == 1
+    assert stats["retried"] == len(Xr)
+    assert np.array_equal(st.cpu().numpy(), st_ref.cpu().numpy())
+    assert np.array_equal(idx.cpu().numpy(), ref.cpu().numpy())
+    # the hook is spent: the next call is normal again
+    L.lagp_knn(dev(X), dev(Xr), 200)
+    assert L.knn_stats()["tc_failed"] == 0
