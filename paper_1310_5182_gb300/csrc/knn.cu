@@ -68,6 +68,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 constexpr int CAND_CAP = 8192;        // candidate capacity cap (sort in shared memory)
+constexpr int SORT_SMALL = 1024;      // survivors the first sort launch holds
 // kNN meta area: the tensor-core screen's failure word (offset 0), two block
 // counters (64), the coordinate bounds (256 and 768, 64 keys each), the
 // launch constants (KnnConst, 1280), then per-query candidate counts and
@@ -657,12 +658,17 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Yv, int p, lagp_d
          const unsigned long long *__restrict__ kmax, const unsigned long long *__restrict__ kmin,
          const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_count, int32_t Cmax,
          int32_t *__restrict__ idx, const KnnConst *__restrict__ kc, const float *__restrict__ rcol,
-         int32_t *__restrict__ retry, int only_retried) {
+         int32_t *__restrict__ retry, int32_t *__restrict__ bigf, int big) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t q = blockIdx.x;
-    // only_retried: the queries that the exact retry recollected; otherwise
-    // every query but those (their rows are written by the second launch)
-    if (retry && (retry[q] != 0) != (only_retried != 0)) return;
+    // Two launches.  The first (big = 0, shared memory for up to 1,024
+    // survivors) sorts every query but those flagged for the exact retry, and
+    // flags (bigf) the ones with more survivors; the second (big = 1, shared
+    // memory for any count) sorts the flagged ones of either kind.
+    const bool flagged = (retry && retry[q] != 0) || (big && bigf[q] != 0);
+    (void)kmax;
+    (void)kmin;
+    if (flagged != (big != 0)) return;
     const int C = cand_count[q];
     const int k = Np ? Np[q] : Npmax;
     int32_t *out = idx + q * Npmax;
@@ -672,12 +678,13 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Yv, int p, lagp_d
     }
     int Cp = 1;
     while (Cp < Cmax) Cp <<= 1;
-    // region 1 (Cp doubles): FP32 keys and rows for steps 1-3, then FP64 keys;
-    // region 2 (Cp words of 64 bits): the survivors' (s, row) keys
+    // region 1 (R1 doubles): FP32 keys and rows for steps 1-3, then FP64 keys;
+    // region 2 (R2 words of 64 bits): the survivors' (s, row) keys
+    const int R1 = big ? Cp : (Cmax + 1) & ~1, R2 = big ? Cp : SORT_SMALL;
     uint32_t *key32 = reinterpret_cast<uint32_t *>(smem_raw);           // Cmax
-    int32_t *rowA = reinterpret_cast<int32_t *>(key32 + Cp);            // Cmax
-    double *dk = reinterpret_cast<double *>(smem_raw);                  // Cp
-    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)Cp * 8);  // Cp
+    int32_t *rowA = reinterpret_cast<int32_t *>(key32 + R1);            // Cmax
+    double *dk = reinterpret_cast<double *>(smem_raw);                  // R1
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)R1 * 8);  // R2
     __shared__ double xq[64];
     __shared__ float yq[64];
     __shared__ float s_d2f;
@@ -786,12 +793,16 @@ knn_sort(const void *__restrict__ X, const float *__restrict__ Yv, int p, lagp_d
     int mine = 0;
     for (int e = threadIdx.x; e < C; e += SORT_THREADS) mine += __uint_as_float(key32[e]) <= tauf;
     int S = 0;
-    int pos = block_excl_scan(mine, wsum, &S);
+    int pos = block_excl_scan(mine, wsum, &S);  // S is block-uniform
+    int Sp = 1;
+    while (Sp < S) Sp <<= 1;
+    if (Sp > R2) {  // more survivors than this launch holds: the second launch sorts it
+        if (threadIdx.x == 0) bigf[q] = 1;
+        return;
+    }
     for (int e = threadIdx.x; e < C; e += SORT_THREADS)
         if (__uint_as_float(key32[e]) <= tauf)
             sk[pos++] = ((unsigned long long)key32[e] << 32) | (uint32_t)rowA[e];
-    int Sp = 1;
-    while (Sp < S) Sp <<= 1;
     for (int e = S + threadIdx.x; e < Sp; e += SORT_THREADS) sk[e] = ~0ull;
     __syncthreads();
     // (4) bitonic sort on (s, row): up to 1,024 keys in registers (four a
@@ -922,7 +933,7 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     cudaStream_t st = ctx->stream;
     ctx->knn_last_M = M;
     const int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
-    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
+    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 12));
     int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
     // sample stride: about 8 N' sampled rows per candidate set, 1 (exact) for small designs
     const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(64, N / (8 * (int64_t)Npmax)));
@@ -939,7 +950,9 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     unsigned long long *kmin = reinterpret_cast<unsigned long long *>(meta + 768);
     int32_t *cc = reinterpret_cast<int32_t *>(meta + META_HEAD);
     int32_t *retry = cc + M;
+    int32_t *bigf = retry + M;  // queries with more survivors than the first sort holds
     LAGP_CUDA(ctx, cudaMemsetAsync(meta, 0, META_HEAD, st));
+    LAGP_CUDA(ctx, cudaMemsetAsync(bigf, 0, (size_t)M * 4, st));
     const int blocks = ctx->num_sms * 4;
     knn_bounds<<<blocks, 256, 0, st>>>(X, N, Xref, M, p, dtype, kmax, kmin);
     KnnConst *kc = reinterpret_cast<KnnConst *>(meta + META_CONST);
@@ -963,9 +976,12 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)ctx->num_sms * 2));
     int Cp = 1;
     while (Cp < Cmax) Cp <<= 1;
-    size_t smem_sort = (size_t)Cp * 16;
-    if (smem_sort > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: N' too large for the sort");
-    cudaFuncSetAttribute(knn_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_sort);
+    // the first sort launch: up to SORT_SMALL survivors (more CTAs per SM);
+    // the second: any count
+    const size_t smem_small = (size_t)((Cmax + 1) & ~1) * 8 + (size_t)SORT_SMALL * 8;
+    const size_t smem_big = (size_t)Cp * 16;
+    if (smem_big > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: N' too large for the sort");
+    cudaFuncSetAttribute(knn_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big);
     auto screen = [&](bool retry_pass) {
         switch (p) {
             case 2: launch_screen<2>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
@@ -974,9 +990,9 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
             default: launch_screen<0>(ctx, retry_pass, grid, smem, Y32, Ys, N, p, Xref, dtype, M, Np, Npmax, kmax, kmin, cand, Cmax, cc, status, stride, retry, counters, tau0); break;
         }
     };
-    auto sort = [&](const float *rc, int32_t *rflags, int only_retried) {
-        knn_sort<<<(unsigned)M, SORT_THREADS, smem_sort, st>>>(X, Yv, p, dtype, Xref, M, Np, Npmax, kmax, kmin,
-                                                               cand, cc, Cmax, idx, kc, rc, rflags, only_retried);
+    auto sort = [&](const float *rc, int32_t *rflags, int big) {
+        knn_sort<<<(unsigned)M, SORT_THREADS, big ? smem_big : smem_small, st>>>(
+            X, Yv, p, dtype, Xref, M, Np, Npmax, kmax, kmin, cand, cc, Cmax, idx, kc, rc, rflags, bigf, big);
         ctx->launches++;
     };
     screen(false);
@@ -992,6 +1008,7 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     } else {
         screen(true);
         sort(nullptr, nullptr, 0);
+        sort(nullptr, nullptr, 1);
     }
     LAGP_CUDA(ctx, cudaGetLastError());
     return LAGP_OK;
@@ -1003,7 +1020,7 @@ lagp_status launch_knn_tc_dist(lagp_ctx *ctx, const void *X, int64_t N, int p, l
                                const void *Xref, int64_t M, float *out) {
     if (!knn_tc_supported(p)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn_tc_dist: p > 20");
     cudaStream_t st = ctx->stream;
-    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 8));
+    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 12));
     void *tc_ws = lagp_ws(ctx, WS_KNN_TC, knn_tc_workspace(N, M, p));
     if (!meta || !tc_ws) return LAGP_ENOMEM;
     unsigned long long *kmax = reinterpret_cast<unsigned long long *>(meta + 256);
