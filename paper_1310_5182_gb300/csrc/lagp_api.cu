@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
@@ -106,6 +107,7 @@ lagp_status lagp_destroy(lagp_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (int s = 0; s < WS_NSLOTS; s++)
         if (ctx->ws[s]) cudaFree(ctx->ws[s]);
+    if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
     delete ctx;
     return LAGP_OK;
 }
@@ -153,6 +155,12 @@ lagp_status lagp_alc_work(lagp_ctx *ctx, uint64_t *out) {
 }
 
 // --------------------------------------------------------------------- kNN
+
+// d0 everywhere, on the device (no host staging, no synchronisation)
+__global__ void fill_f64_kernel(double *p, int64_t n, double v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
 
 static lagp_status check_design(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
                                 lagp_dtype dtype, const char *fn) {
@@ -370,12 +378,10 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
     LAGP_CUDA(ctx, cudaMemcpyAsync(dR, Xref, M * p * es, cudaMemcpyHostToDevice, st));
     if (Nprime) LAGP_CUDA(ctx, cudaMemcpyAsync(dNp, Nprime, M * 4, cudaMemcpyHostToDevice, st));
     if (n) LAGP_CUDA(ctx, cudaMemcpyAsync(dn, n, M * 4, cudaMemcpyHostToDevice, st));
-    // d starts at d0 everywhere: fill on the host side of a small staging copy
-    {
-        std::vector<double> h(M, d0);
-        LAGP_CUDA(ctx, cudaMemcpyAsync(dd, h.data(), M * 8, cudaMemcpyHostToDevice, st));
-        LAGP_CUDA(ctx, cudaStreamSynchronize(st));  // h leaves scope
-    }
+    // d starts at d0 everywhere
+    fill_f64_kernel<<<(unsigned)std::min<int64_t>((M + 255) / 256, 1024), 256, 0, st>>>(dd, M, d0);
+    ctx->launches++;
+    LAGP_CUDA(ctx, cudaGetLastError());
     LAGP_TRY(lagp_knn(ctx, dX, N, p, dtype, dR, M, dNp, Nprime_max, dIdx, dSt(0)));
     if (mle_rounds > 0) {
         // Fig. 1 steps 2-3, repeated (step 4): design at the current d, MLE of
@@ -400,9 +406,18 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
     LAGP_CUDA(ctx, cudaMemcpyAsync(s2, dS2, M * 8, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaMemcpyAsync(df, dDf, M * 8, cudaMemcpyDeviceToHost, st));
     if (d_out) LAGP_CUDA(ctx, cudaMemcpyAsync(d_out, dd, M * 8, cudaMemcpyDeviceToHost, st));
-    std::vector<int32_t> sv((size_t)nst * M);
+    // the stages' statuses through the context's pinned staging buffer
+    const size_t sv_bytes = (size_t)nst * M * 4;
+    if (ctx->host_pin_bytes < sv_bytes) {
+        if (ctx->host_pin) cudaFreeHost(ctx->host_pin);
+        ctx->host_pin = nullptr;
+        ctx->host_pin_bytes = 0;
+        LAGP_CUDA(ctx, cudaHostAlloc(&ctx->host_pin, sv_bytes, cudaHostAllocDefault));
+        ctx->host_pin_bytes = sv_bytes;
+    }
+    int32_t *sv = static_cast<int32_t *>(ctx->host_pin);
     for (int i = 0; i < nst; i++)
-        LAGP_CUDA(ctx, cudaMemcpyAsync(sv.data() + (size_t)i * M, dSt(i), M * 4, cudaMemcpyDeviceToHost, st));
+        LAGP_CUDA(ctx, cudaMemcpyAsync(sv + (size_t)i * M, dSt(i), M * 4, cudaMemcpyDeviceToHost, st));
     LAGP_CUDA(ctx, cudaStreamSynchronize(st));
     // first failing stage wins: kNN, then each round's selection and MLE, then prediction
     for (int64_t m = 0; m < M; m++) {

@@ -40,6 +40,8 @@ struct lagp_ctx {
     bool work_zeroed = false;  // ALC work counters cleared once after allocation
     int64_t knn_last_M = 0;    // queries of the last lagp_knn call (for lagp_knn_stats)
     int knn_tc_stall = 0;      // test hook for the next tensor-core kNN pass (lagp_knn_tc_stall)
+    void *host_pin = nullptr;  // pinned host staging (lagp_agp's statuses), grown on demand
+    size_t host_pin_bytes = 0;
 };
 
 // Shape key of an ALC launch for the autotuner's table.

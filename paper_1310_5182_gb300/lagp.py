@@ -480,10 +480,15 @@ def lagp_agp(X, Y, Xref, n0, n, Nprime, d0, g, prec="f32bulk", mle=None, rounds=
     Xref = np.ascontiguousarray(Xref, dtype=X.dtype)
     N, p = X.shape
     M = Xref.shape[0]
-    n_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(n, np.int32), (M,)))
-    Np_arr = np.ascontiguousarray(np.broadcast_to(np.asarray(Nprime, np.int32), (M,)))
-    out = {k: np.empty(M, np.float64) for k in ("mean", "s2", "df", "d")}
-    status = np.empty(M, np.int32)
+    # per-location sizes and the outputs in pinned host memory (torch's caching
+    # host allocator): the library's copies to and from them run at full rate
+    pinned = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    n_arr = pinned(M, torch.int32)
+    n_arr[:] = np.broadcast_to(np.asarray(n, np.int32), (M,))
+    Np_arr = pinned(M, torch.int32)
+    Np_arr[:] = np.broadcast_to(np.asarray(Nprime, np.int32), (M,))
+    out = {k: pinned(M, torch.float64) for k in ("mean", "s2", "df", "d")}
+    status = pinned(M, torch.int32)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     dmin, dmax, it = mle if mle is not None else (1e-3, 20.0, 0)
     _check(_lib.lagp_agp(ctx, ptr(X), ptr(Y), N, p, LAGP_F64 if X.dtype == np.float64 else LAGP_F32,
