@@ -138,3 +138,26 @@ def test_bounded_wait_reports_and_retries(L):
     # the hook is spent: the next call is normal again
     L.lagp_knn(dev(X), dev(Xr), 200)
     assert L.knn_stats()["tc_failed"] == 0
+
+
+def test_non_finite_rows_both_paths(L):
+    """Design rows with NaN or infinite coordinates never enter a candidate
+    set on either path; the two paths agree bit for bit (statuses too)."""
+    rng = np.random.default_rng(43)
+    X = rng.uniform(0, 1, (6_000, 8))
+    X[[3, 500, 4_999], 2] = np.nan
+    X[[10, 2_000], 5] = np.inf
+    X[[77], 0] = -np.inf
+    Xr = rng.uniform(0, 1, (33, 8))
+    L.set_tuning(knn_path=0)
+    idx_tc, st_tc = L.lagp_knn(dev(X), dev(Xr), 300)
+    L.set_tuning(knn_path=1)
+    try:
+        idx_cc, st_cc = L.lagp_knn(dev(X), dev(Xr), 300)
+    finally:
+        L.set_tuning(knn_path=0)
+    bad = {3, 500, 4_999, 10, 2_000, 77}
+    assert not bad & set(idx_tc.cpu().numpy().ravel().tolist())
+    assert np.array_equal(idx_tc.cpu().numpy(), idx_cc.cpu().numpy())
+    assert np.array_equal(st_tc.cpu().numpy(), st_cc.cpu().numpy())
+    assert (st_tc.cpu().numpy() == 0).all()

@@ -105,7 +105,8 @@ def compare_selection(gpu_sel, ref, n_arr, n0, g, gap_rel=NEAR_TIE):
 # ------------------------------------------------------------------ kNN (a1)
 
 @pytest.mark.parametrize("case", ["toy2d_full", "borehole8d", "slab3d_f32", "ragged", "lattice_ties",
-                                  "offset_small_spread", "far_clusters"])
+                                  "offset_small_spread", "far_clusters", "p20_tensor_cores",
+                                  "p24_cuda_cores"])
 def test_knn_bit_exact(L, O, case):
     rng = np.random.default_rng(21)
     Np_arr = None
@@ -133,6 +134,14 @@ def test_knn_bit_exact(L, O, case):
         X = np.concatenate([c + 1e-3 * rng.standard_normal((2_000, 3)) for c in centres])
         Xr = np.concatenate([c + 1e-3 * rng.standard_normal((6, 3)) for c in centres])
         Npm = 500
+    elif case == "p20_tensor_cores":  # the widest rows of the tensor-core collection (K = 64)
+        X = rng.uniform(0, 1, (12_000, 20))
+        Xr = rng.uniform(0, 1, (23, 20))
+        Npm = 300
+    elif case == "p24_cuda_cores":    # beyond the tensor-core rows: CUDA-core collection
+        X = rng.uniform(0, 1, (9_000, 24))
+        Xr = rng.uniform(0, 1, (19, 24))
+        Npm = 250
     else:                             # a lattice: many exact distance ties
         g = np.arange(40, dtype=np.float64)
         X = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2)
