@@ -35,9 +35,10 @@
 // four groups of four epilogue warps (one per TMEM lane quarter; group g
 // takes the design blocks it = g mod 4, accumulator g) read the distances
 // back.  A lane compares its design row's distances with the queries'
-// thresholds into a bit mask (two instructions a pair); only the set bits
-// (about 1.5% of the pairs) are visited to append the row to the query's
-// candidate list.
+// thresholds into a bit mask, two columns per FP16 x 2 compare (values
+// rounded down, thresholds up: no hit is lost); only the set bits (about
+// 1.5% of the pairs) are visited to append the row to the query's candidate
+// list.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -68,10 +69,18 @@ __device__ __forceinline__ int64_t tc_off(int64_t r, int k, int K) {
     return (r >> 3) * (8 * (int64_t)K) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-// all ones when a <= b, else zero (NaN: zero)
-__device__ __forceinline__ uint32_t le_mask(float a, float b) {
+// Two FP32 values as FP16 x 2, rounded toward zero with negatives clamped to
+// zero (never above the value they stand for, for a value >= 0; NaN stays
+// NaN): x in the low half, y in the high half.
+__device__ __forceinline__ uint32_t f16x2_rz_relu(float x, float y) {
     uint32_t r;
-    asm("set.le.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    asm("cvt.rz.relu.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(y), "f"(x));
+    return r;
+}
+// per half: 0xFFFF when a <= b, else 0 (NaN: 0)
+__device__ __forceinline__ uint32_t le_mask_h2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("set.le.u32.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
     return r;
 }
 
@@ -171,8 +180,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
     __half *sA = reinterpret_cast<__half *>(smem_raw);         // S stages x 128 rows
     __half *sQ = sA + (size_t)S * stage_halves;                // TC_QMAX rows
     float *s_tau2 = reinterpret_cast<float *>(sQ + (size_t)TC_QMAX * K);  // TC_QMAX
-    int *s_cnt = reinterpret_cast<int *>(s_tau2 + TC_QMAX);   // TC_QMAX
-    uint32_t *s_que = reinterpret_cast<uint32_t *>(s_cnt + TC_QMAX);  // per epilogue warp: TC_QUE entries
+    uint32_t *s_t2h = reinterpret_cast<uint32_t *>(s_tau2 + TC_QMAX);  // TC_QMAX/2: FP16 x 2, rounded up
+    int *s_cnt = reinterpret_cast<int *>(s_t2h + TC_QMAX / 2);       // TC_QMAX
+    uint2 *s_que = reinterpret_cast<uint2 *>(s_cnt + TC_QMAX);  // per epilogue warp: TC_QUE entries
     uint64_t *bar = reinterpret_cast<uint64_t *>(s_que + TC_QUE * 4 * TC_EPI_GROUPS);
     uint64_t *full = bar, *empty = bar + S, *tfull = bar + 2 * S, *tempty = bar + 2 * S + TC_NACC;
     __shared__ uint32_t s_tmem;
@@ -235,6 +245,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
             s_tau2[c] = t2 * s2;  // an exact scaling
             s_cnt[c] = 0;
         }
+        __syncthreads();
+        // the thresholds in FP16, rounded up (so that a value below a threshold
+        // stays below it after both roundings), two a word
+        for (int c2 = tid; c2 < TC_QMAX / 2; c2 += TC_THREADS) {
+            const float ta = s_tau2[2 * c2], tb = s_tau2[2 * c2 + 1];
+            const __half ha = __float2half_ru(ta), hb = __float2half_ru(tb);
+            s_t2h[c2] = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+        }
         fence_proxy_async_smem();
         __syncthreads();
 
@@ -288,7 +306,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
             // epilogue: group g reads accumulator g, of the design blocks with
             // it = g (mod 4); each warp its TMEM lane quarter (32 design rows)
             const int g = (warp - 2) >> 2, quarter = warp & 3;
-            uint32_t *que = s_que + (size_t)(warp - 2) * TC_QUE;
+            uint2 *que = s_que + (size_t)(warp - 2) * TC_QUE;
             const uint32_t lt_mask = (1u << lane) - 1u;
             for (int mb = 0; mb < a.nmb; mb++) {
                 const long long it = it0 + mb;
@@ -328,33 +346,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) knn_screen_tc(TcArgs a) {
                                         a.dump[(q0 + c0 + i) * a.N + row] = __uint_as_float(v[h][i]) / s2;
                             continue;
                         }
-                        // hit mask: bit i set when s <= tau2 of query c0 + i (NaN never)
-                        const float4 *t4 = reinterpret_cast<const float4 *>(s_tau2 + c0);
-                        uint32_t m = 0;
+                        // hit mask, compared two columns a time in FP16 (values
+                        // rounded down, thresholds up: no hit is lost; the
+                        // rounding admits at most a few extra rows): column
+                        // c0 + 2i sets bit i, column c0 + 2i + 1 bit 16 + i
+                        const uint4 *t4 = reinterpret_cast<const uint4 *>(s_t2h + c0 / 2);
+                        uint32_t m2 = 0;
 #pragma unroll
-                        for (int i4 = 0; i4 < 4; i4++) {
-                            const float4 t = t4[i4];
-                            m |= le_mask(__uint_as_float(v[h][4 * i4 + 0]), t.x) & (1u << (4 * i4 + 0));
-                            m |= le_mask(__uint_as_float(v[h][4 * i4 + 1]), t.y) & (1u << (4 * i4 + 1));
-                            m |= le_mask(__uint_as_float(v[h][4 * i4 + 2]), t.z) & (1u << (4 * i4 + 2));
-                            m |= le_mask(__uint_as_float(v[h][4 * i4 + 3]), t.w) & (1u << (4 * i4 + 3));
+                        for (int i4 = 0; i4 < 2; i4++) {
+                            const uint4 t = t4[i4];
+                            const uint32_t tt[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                            for (int q2 = 0; q2 < 4; q2++) {
+                                const int i = 4 * i4 + q2;  // the pair of columns c0 + 2i, c0 + 2i + 1
+                                const uint32_t hv = f16x2_rz_relu(__uint_as_float(v[h][2 * i]), __uint_as_float(v[h][2 * i + 1]));
+                                m2 |= le_mask_h2(hv, tt[q2]) & (0x00010001u << i);
+                            }
                         }
-                        if (!live) m = 0u;
-                        // a lane with hits queues (chunk, lane, mask); the
+                        if (!live) m2 = 0u;
+                        // a lane with hits queues (chunk and lane, mask); the
                         // queue is drained lane-parallel after the block
-                        const uint32_t b = __ballot_sync(LAGP_FULL_MASK, m != 0u);
-                        if (m) que[qn + __popc(b & lt_mask)] = ((uint32_t)(c0 >> 4) << 21) | ((uint32_t)lane << 16) | m;
+                        const uint32_t b = __ballot_sync(LAGP_FULL_MASK, m2 != 0u);
+                        if (m2) que[qn + __popc(b & lt_mask)] = make_uint2(((uint32_t)(c0 >> 4) << 5) | (uint32_t)lane, m2);
                         qn += __popc(b);
                     }
                 }
                 __syncwarp();
                 for (int e = lane; e < qn; e += 32) {
-                    const uint32_t w = que[e];
-                    const int cb0 = (int)(w >> 21) * 16;
-                    const int32_t hrow = (int32_t)(mb * TC_MROWS + quarter * 32 + ((w >> 16) & 31u));
-                    uint32_t mm = w & 0xFFFFu;
+                    const uint2 w = que[e];
+                    const int cb0 = (int)(w.x >> 5) * 16;
+                    const int32_t hrow = (int32_t)(mb * TC_MROWS + quarter * 32 + (w.x & 31u));
+                    uint32_t mm = w.y;  // bit i: column cb0 + 2i; bit 16 + i: column cb0 + 2i + 1
                     while (mm) {
-                        const int c = cb0 + __ffs(mm) - 1;
+                        const int bit = __ffs(mm) - 1;
+                        const int c = cb0 + (bit < 16 ? 2 * bit : 2 * (bit - 16) + 1);
                         mm &= mm - 1u;
                         const int pos = atomicAdd(&s_cnt[c], 1);
                         if (pos < a.Cmax) a.cand[(q0 + c) * a.Cmax + pos] = hrow;
@@ -471,12 +496,13 @@ lagp_status launch_knn_tc_collect(lagp_ctx *ctx, void *ws, int64_t N, int p, int
     a.nblocks = (int)((M + a.nq - 1) / a.nq);
     // as many stages as fit (at most TC_STAGES_MAX): the CTA then has the SM
     // (and its tensor memory) to itself
-    const size_t fixed = (size_t)TC_QMAX * K * 2 + (2 * TC_QMAX + TC_QUE * 4 * TC_EPI_GROUPS) * 4 +
+    const size_t fixed = (size_t)TC_QMAX * K * 2 + (2 * TC_QMAX + TC_QMAX / 2 + 2 * TC_QUE * 4 * TC_EPI_GROUPS) * 4 +
                          (2 * TC_STAGES_MAX + 2 * TC_NACC) * 8 + 1024;
     const size_t stage_bytes = (size_t)TC_MROWS * K * 2;
     a.stages = (int)std::min<size_t>(TC_STAGES_MAX, (ctx->smem_optin - fixed) / stage_bytes);
     if (a.stages < 2) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: tensor-core screen exceeds shared memory");
-    size_t smem = (size_t)a.stages * stage_bytes + (size_t)TC_QMAX * K * 2 + (2 * TC_QMAX + TC_QUE * 4 * TC_EPI_GROUPS) * 4 +
+    size_t smem = (size_t)a.stages * stage_bytes + (size_t)TC_QMAX * K * 2 +
+                  (2 * TC_QMAX + TC_QMAX / 2 + 2 * TC_QUE * 4 * TC_EPI_GROUPS) * 4 +
                   (2 * (size_t)a.stages + 2 * TC_NACC) * 8;
     // more than half of the SM's shared memory: one CTA per SM, which then
     // holds the whole tensor memory
