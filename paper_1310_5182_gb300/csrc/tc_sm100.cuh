@@ -115,14 +115,6 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lb
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor of kind::tf32 with FP32 accumulation, both operands
-// TF32 and K-major: D format F32 (1) at [4,6), A format TF32 (2) at [7,10),
-// B format TF32 (2) at [10,13), no negation or transposition, N >> 3 at
-// [17,23), M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t idesc_tf32_f32(int m, int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-
 // Instruction descriptor of kind::f16 with FP32 accumulation, both operands
 // F16 (format 0) and K-major: D format F32 (1) at [4,6), N >> 3 at [17,23),
 // M >> 4 at [24,29).
@@ -142,16 +134,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 // arrives once on `bar` when every tcgen05 operation this thread issued so
 // far has completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
