@@ -140,6 +140,8 @@ struct F32Params {
     int num_sms;      // the co-resident CTAs of an SM are blockIdx.x, + num_sms, + 2 num_sms, ...
     int tmax;         // rescore_max
     float rel;        // rescore_rel (cap of the contender margin)
+    int etab_smem;    // 1: the exp table copied to shared memory; 0: read through L1 (when
+                      // the copy would cost the SM a resident CTA)
 };
 
 // Contenders kept in the first (static) part of the appended list; at least
@@ -222,8 +224,8 @@ alc_bulk_kernel(F32Params P) {
     double *kx = Kinv + (size_t)(nmax + 1) * ld;                // nmax (even): k_j(x)
     double *xd = kx + ((nmax + 1) & ~1);                        // nmax x p: design coordinates
     double *xq = xd + (size_t)nmax * p;                         // p (even): reference location
-    double *etab = xq + ((p + 1) & ~1);                         // EXP64_TABLE_SIZE: table of exp64_tang
-    double *con_k = etab + EXP64_TABLE_SIZE;                                  // tmax x ld: k_j(x_c), FP64
+    double *etab_s = xq + ((p + 1) & ~1);                       // EXP64_TABLE_SIZE (or 0): exp table
+    double *con_k = etab_s + (P.etab_smem ? EXP64_TABLE_SIZE : 0);  // tmax x ld: k_j(x_c), FP64
     double *con_b = con_k + (size_t)tmax * ld;                  // tmax x ld: K^{-1} k_j(x_c)
     double *cpart = con_b + (size_t)tmax * ld;                  // max(8,tmax) x ld partials;
                                                                 // row 0 then holds mu b of the winner
@@ -260,7 +262,9 @@ alc_bulk_kernel(F32Params P) {
     // (warp w runs on sub-partition w mod 4)
     const int rot = (blockIdx.x / P.num_sms) & 3;
     const int lead = 32 * rot;  // the thread with the CTA's scalar duties
-    for (int i = tid; i < EXP64_TABLE_SIZE; i += F32_THREADS) etab[i] = exp64_table_g[i];
+    const double *etab = P.etab_smem ? etab_s : exp64_table_g;  // table of exp64_tang
+    if (P.etab_smem)
+        for (int i = tid; i < EXP64_TABLE_SIZE; i += F32_THREADS) etab_s[i] = exp64_table_g[i];
     if (tid < 4) s_work[tid] = 0ull;
 
     for (;;) {
@@ -766,14 +770,23 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     const size_t nmax = (size_t)a.nmax, p = (size_t)a.p;
     const size_t ld = (nmax + 3) & ~(size_t)1;
     const size_t union_doubles = std::max((size_t)Npad, (2 * (size_t)tmax + std::max(F32_WARPS, tmax)) * ld);
-    const size_t smem = 8 * ((nmax + 1) * ld + ((nmax + 1) & ~(size_t)1) + nmax * p + ((p + 1) & ~(size_t)1) +
-                             EXP64_TABLE_SIZE + union_doubles) +
-                        sizeof(T) * (ld + p);
-    if (smem > ctx->smem_optin)
+    const size_t smem_notab = 8 * ((nmax + 1) * ld + ((nmax + 1) & ~(size_t)1) + nmax * p +
+                                   ((p + 1) & ~(size_t)1) + union_doubles) +
+                              sizeof(T) * (ld + p);
+    const size_t smem_tab = smem_notab + 8 * (size_t)EXP64_TABLE_SIZE;
+    if (smem_notab > ctx->smem_optin)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory exceeded (n_max, p too large)");
-    cudaFuncSetAttribute(alc_bulk_kernel<CPT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_bulk_kernel<CPT, T>, F32_THREADS, smem);
+    // the exp table goes to shared memory unless that costs a resident CTA
+    // (large n_max: the table's 8 KB decide between one and two CTAs an SM)
+    int occ = 0, occ_notab = 0;
+    cudaFuncSetAttribute(alc_bulk_kernel<CPT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)std::min(smem_tab, (size_t)ctx->smem_optin));
+    if (smem_tab <= ctx->smem_optin)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_bulk_kernel<CPT, T>, F32_THREADS, smem_tab);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_notab, alc_bulk_kernel<CPT, T>, F32_THREADS, smem_notab);
+    const int etab_smem = occ > 0 && occ >= occ_notab ? 1 : 0;
+    const size_t smem = etab_smem ? smem_tab : smem_notab;
+    if (!etab_smem) occ = occ_notab;
     const bool f64state = sizeof(T) == 8;
     int per_sm = alc_ctas_per_sm(ctx, alc_shape_key(f64state ? "alc_f64schur" : "alc_f32", CPT, a.nmax, a.p,
                                                     a.mean != nullptr),
@@ -789,7 +802,8 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     LAGP_TRY(alc_counters(ctx, &counter, &work));
     if (!U) return LAGP_ENOMEM;
     LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    F32Params P{a, counter, work, U, U + U_elems, Npad, ctx->num_sms, tmax, (float)ctx->tuning.rescore_rel};
+    F32Params P{a, counter, work, U, U + U_elems, Npad, ctx->num_sms, tmax, (float)ctx->tuning.rescore_rel,
+                etab_smem};
     alc_bulk_kernel<CPT, T><<<(unsigned)grid, F32_THREADS, smem, st>>>(P);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());

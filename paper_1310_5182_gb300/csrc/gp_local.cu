@@ -62,39 +62,75 @@ __device__ void block_sums(double (&v)[NV], const Blk &b) {
     for (int i = 0; i < NV; i++) v[i] = tot[i];
 }
 
-// Lower Cholesky of the symmetric n x n matrix A (lower triangle used) into L,
-// left-looking, with rd = 1 / diag(L).  Returns false (block-uniform) if a
-// pivot is not positive.
-__device__ bool block_cholesky(const double *A, double *L, double *rd, int n, int ld, int *flag,
-                               const Blk &b) {
-    if (b.tid == 0) *flag = 1;
+// Lower Cholesky factor L of the symmetric n x n matrix A (lower triangle
+// used), rd = 1 / diag(L), and in the same sweep the forward solves
+// z_r = L^{-1} b_r of NR right-hand sides: each b_r^T is one more row of the
+// factorised matrix (factorising [[A, B^T], [B, .]] gives the rows B L^{-T},
+// that is z_r^T).  Left-looking by columns with one barrier per column: in
+// the phase of column c every row i >= c (and every right-hand side) forms
+//   s_i = A[i][c] - sum_{k<c} L[i][k] L[c][k];
+// the pivot row takes L[c][c] = sqrt(s_c) and rd[c], the other rows keep s_i
+// unscaled in a double buffer, and each row scales its own entry of column
+// c by rd[c] in the next phase, whose sums take their term k = c from that
+// buffer.  A phase therefore needs no second barrier, and no reduction: the
+// pivot's sum is one lane's.  ub: 2 (n + NR) doubles of shared memory.
+// Returns false (block-uniform) if a pivot is not positive.
+// Entry r of a small array of pointers without indexing it at run time (no
+// local-memory copy of the array).
+template <int NR, typename P>
+__device__ __forceinline__ P pick(P const (&v)[NR], int r) {
+    P x = v[0];
+#pragma unroll
+    for (int q = 1; q < NR; q++)
+        if (r == q) x = v[q];
+    return x;
+}
+
+template <int NR>
+__device__ bool block_cholesky(const double *A, double *L, double *rd, int n, int ld,
+                               const double *const (&b)[NR], double *const (&z)[NR], double *ub,
+                               int *flag, const Blk &bk) {
+    const int rows = n + NR;
+    if (bk.tid == 0) *flag = 1;
     for (int c = 0; c < n; c++) {
-        if (b.warp == 0) {
-            double s = 0.0;
-            for (int k = b.lane; k < c; k += 32) s = fma(L[(size_t)c * ld + k], L[(size_t)c * ld + k], s);
-            s = warp_sum(s);
-            if (b.lane == 0) {
-                double piv = A[(size_t)c * ld + c] - s;
-                if (!(piv > 0.0)) *flag = 0;
-                const double lcc = piv > 0.0 ? sqrt(piv) : 1.0;
-                L[(size_t)c * ld + c] = lcc;
-                rd[c] = 1.0 / lcc;  // once, not in every thread (the FP64 unit is the bound)
+        const double *prev = ub + ((c + 1) & 1) * rows;  // column c - 1, unscaled
+        double *cur = ub + (c & 1) * rows;
+        const double rdp = c > 0 ? rd[c - 1] : 0.0;
+        const double lcp = c > 0 ? prev[c] * rdp : 0.0;  // L[c][c-1]
+        const double *Lc = L + (size_t)c * ld;
+        for (int i = c + bk.tid; i < rows; i += GP_THREADS) {
+            double *Lr = i < n ? L + (size_t)i * ld : pick(z, i - n);
+            double s0 = i < n ? A[(size_t)i * ld + c] : pick(b, i - n)[c], s1 = 0.0;
+            if (c > 0) {
+                const double u = prev[i] * rdp;  // L[i][c-1]: scaled by its own row
+                Lr[c - 1] = u;
+                s0 = fma(-u, lcp, s0);
             }
-        }
-        __syncthreads();
-        const double rcc = rd[c];
-        for (int i = c + 1 + b.tid; i < n; i += GP_THREADS) {
-            double s0 = A[(size_t)i * ld + c], s1 = 0.0;
             int k = 0;
-            for (; k + 2 <= c; k += 2) {  // two chains: half the dependent FMA latency
-                s0 = fma(-L[(size_t)i * ld + k], L[(size_t)c * ld + k], s0);
-                s1 = fma(-L[(size_t)i * ld + k + 1], L[(size_t)c * ld + k + 1], s1);
+            for (; k + 2 <= c - 1; k += 2) {  // two chains: half the dependent FMA latency
+                s0 = fma(-Lr[k], Lc[k], s0);
+                s1 = fma(-Lr[k + 1], Lc[k + 1], s1);
             }
-            if (k < c) s0 = fma(-L[(size_t)i * ld + k], L[(size_t)c * ld + k], s0);
-            L[(size_t)i * ld + c] = (s0 + s1) * rcc;
+            if (k < c - 1) s0 = fma(-Lr[k], Lc[k], s0);
+            const double s = s0 + s1;
+            if (i == c) {
+                if (!(s > 0.0)) *flag = 0;
+                const double r = s > 0.0 ? rsqrt(s) : 1.0;
+                L[(size_t)c * ld + c] = s > 0.0 ? s * r : 1.0;
+                rd[c] = r;
+            } else {
+                cur[i] = s;
+            }
         }
         __syncthreads();
     }
+    // the scaling of the last column: only the right-hand sides have entries
+    // below its diagonal
+    if (n > 0) {
+        const double *last = ub + ((n - 1) & 1) * rows;
+        if (bk.tid < NR) pick(z, bk.tid)[n - 1] = last[n + bk.tid] * rd[n - 1];
+    }
+    __syncthreads();
     return *flag != 0;
 }
 
@@ -199,51 +235,50 @@ __device__ void build_K(const double *D, int nm, int ld, double d, double g, dou
     __syncthreads();
 }
 
-// log-likelihood of Eq. (gpk) at d: needs K built; leaves L and a = K^{-1} y.
-// Returns false if K is not positive definite.
-__device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, double *a, double *tmp,
-                           double *rd, double *red, int *flag, double *out_l, double *out_psi,
-                           const Blk &b) {
-    if (!block_cholesky(W.K, W.L, rd, nm, ld, flag, b)) return false;
-    if (b.warp == 0) {
-        warp_forward(W.L, ld, rd, y, tmp, nm, b.lane);
-        warp_backward(W.L, ld, rd, tmp, a, nm, b.lane);
-    }
-    __syncthreads();
-    double ld_part = 0.0, psi_part = 0.0;
+// log-likelihood of Eq. (gpk) at d: needs K built; leaves L, rd and
+// z = L^{-1} y (psi = y^T K^{-1} y = z^T z).  Returns false if K is not
+// positive definite.
+__device__ bool llik_value(const GpWork &W, int nm, int ld, const double *y, double *z, double *rd,
+                           double *ub, int *flag, double *out_l, double *out_psi, const Blk &b) {
+    const double *const rhs[1] = {y};
+    double *const zs[1] = {z};
+    if (!block_cholesky<1>(W.K, W.L, rd, nm, ld, rhs, zs, ub, flag, b)) return false;
+    double v[2] = {0.0, 0.0};  // log|K|, psi
     for (int i = b.tid; i < nm; i += GP_THREADS) {
-        ld_part += 2.0 * log(W.L[(size_t)i * ld + i]);
-        psi_part += y[i] * a[i];
+        v[0] += 2.0 * log(W.L[(size_t)i * ld + i]);
+        v[1] = fma(z[i], z[i], v[1]);
     }
-    const double logdet = block_sum(ld_part, red, b);
-    const double psi = block_sum(psi_part, red, b);
+    block_sums<2>(v, b);
     // the constant and the logarithms on one thread (every thread evaluating
     // lgamma would hold the FP64 unit for nothing), then broadcast
     __shared__ double s_l;
     if (b.tid == 0) {
         const double hn = 0.5 * nm;
-        s_l = lgamma(hn) - hn * log(2.0 * CUDART_PI) - 0.5 * logdet - hn * log(psi / 2.0);
+        s_l = lgamma(hn) - hn * log(2.0 * CUDART_PI) - 0.5 * v[0] - hn * log(v[1] / 2.0);
     }
     __syncthreads();
     *out_l = s_l;
-    *out_psi = psi;
+    *out_psi = v[1];
     return true;
 }
 
-// K^{-1} from L (needs L and rd = 1 / diag(L)): Li = L^{-1} row by row, the
-// columns of a row in parallel (full-lane FMAs, no reductions), then
-// Ki = Li^T Li.
-__device__ void inverse_from_L(const GpWork &W, int nm, int ld, const double *rd, const Blk &b) {
+// K^{-1} and a = K^{-1} y from L (with rd = 1 / diag(L)) and z = L^{-1} y:
+// Li = L^{-1} row by row, the columns of a row in parallel (full-lane FMAs,
+// no reductions; the sums run down the rows, so that a warp's lanes read one
+// row of Li at a time), then Ki = Li^T Li and a = Li^T z.
+__device__ void inverse_from_L(const GpWork &W, int nm, int ld, const double *rd, const double *z,
+                               double *a, const Blk &b) {
     for (int i = 0; i < nm; i++) {
         const double *Lr = W.L + (size_t)i * ld;
+        // Li[i][c] = (delta_ic - sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
         for (int c = b.tid; c <= i; c += GP_THREADS) {
             double s0 = (c == i) ? 1.0 : 0.0, s1 = 0.0;
-            int k = c;
-            for (; k + 2 <= i; k += 2) {  // Li[i][c] = (delta_ic - sum_{k=c}^{i-1} L[i][k] Li[k][c]) / L[i][i]
+            int k = i - 1;
+            for (; k - 1 >= c; k -= 2) {
                 s0 = fma(-Lr[k], W.Li[(size_t)k * ld + c], s0);
-                s1 = fma(-Lr[k + 1], W.Li[(size_t)(k + 1) * ld + c], s1);
+                s1 = fma(-Lr[k - 1], W.Li[(size_t)(k - 1) * ld + c], s1);
             }
-            if (k < i) s0 = fma(-Lr[k], W.Li[(size_t)k * ld + c], s0);
+            if (k >= c) s0 = fma(-Lr[k], W.Li[(size_t)k * ld + c], s0);
             W.Li[(size_t)i * ld + c] = (s0 + s1) * rd[i];
         }
         __syncthreads();
@@ -261,6 +296,16 @@ __device__ void inverse_from_L(const GpWork &W, int nm, int ld, const double *rd
         W.Ki[(size_t)i * ld + k] = s0 + s1;
         W.Ki[(size_t)k * ld + i] = s0 + s1;
     }
+    for (int k = b.tid; k < nm; k += GP_THREADS) {  // a[k] = sum_{i >= k} Li[i][k] z[i]
+        double s0 = 0.0, s1 = 0.0;
+        int i = nm - 1;
+        for (; i - 1 >= k; i -= 2) {
+            s0 = fma(W.Li[(size_t)i * ld + k], z[i], s0);
+            s1 = fma(W.Li[(size_t)(i - 1) * ld + k], z[i - 1], s1);
+        }
+        if (i >= k) s0 = fma(W.Li[(size_t)i * ld + k], z[i], s0);
+        a[k] = s0 + s1;
+    }
     __syncthreads();
 }
 
@@ -268,17 +313,23 @@ struct Derivs {
     double dl, d2l, dldg, trKi;
 };
 
-// First and second d-derivatives of l (and dl/dg); needs K, L, a, psi.
-// The two traces with K' come from one of two products:
+// First and second d-derivatives of l (and dl/dg); needs K, L, rd, z = L^{-1} y
+// and psi; leaves a = K^{-1} y.  The two traces with K' come from one of two
+// products:
 //   L_FREE (L is not needed afterwards): K' in A1's storage, C = L^{-1} K'
-//     into L's storage (n^3/2 FMAs), and B = C L^{-T} = L^{-1} K' L^{-T}
-//     (symmetric) over its lower triangle only (n^3/6), never stored:
-//     tr(K^{-1} K') = tr(B), tr(K^{-1} K' K^{-1} K') = |B|_F^2;
+//     (n^3/2 FMAs) stored transposed in L's storage, and B = C L^{-T} =
+//     L^{-1} K' L^{-T} (symmetric) over its lower triangle only (n^3/6),
+//     column by column so that the lanes of a warp share the length of their
+//     sums, never stored: tr(K^{-1} K') = tr(B), tr(K^{-1} K' K^{-1} K') =
+//     |B|_F^2;
 //   otherwise: K' in Li's storage once K^{-1} is built, A1 = K^{-1} K' (n^3).
+// The symmetric matrices K', K'' and K^{-1} are read by columns where that
+// makes a warp's loads contiguous, and the sums over them run over the lower
+// triangle (off-diagonal entries twice).
 template <bool L_FREE>
-__device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const double *a, double psi,
-                              const double *rd, double *t1, double *t2, double *red, const Blk &b) {
-    inverse_from_L(W, nm, ld, rd, b);
+__device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const double *z, double *a,
+                              double psi, const double *rd, double *t1, double *t2, const Blk &b) {
+    inverse_from_L(W, nm, ld, rd, z, a, b);
     const double id2 = 1.0 / (d * d), id3 = id2 / d, id4 = id2 * id2;
     double *Kp = L_FREE ? W.A1 : W.Li;
     for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
@@ -289,8 +340,8 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
     __syncthreads();
     double trA1 = 0.0, trA1A1 = 0.0;
     if constexpr (L_FREE) {
-        // C = L^{-1} K': C[i][k] = sum_{m <= i} Li[i][m] K'[m][k]
-        double *Cm = W.L;
+        // C = L^{-1} K': C[i][k] = sum_{m <= i} Li[i][m] K'[m][k], into Ct[k][i]
+        double *Ct = W.L;
         for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
             const int i = e / nm, k = e - i * nm;
             const double *Lir = W.Li + (size_t)i * ld;
@@ -301,21 +352,23 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
                 s1 = fma(Lir[m + 1], Kp[(size_t)(m + 1) * ld + k], s1);
             }
             if (m <= i) s0 = fma(Lir[m], Kp[(size_t)m * ld + k], s0);
-            Cm[(size_t)i * ld + k] = s0 + s1;
+            Ct[(size_t)k * ld + i] = s0 + s1;
         }
         __syncthreads();
-        // B[i][j] = sum_{k <= j} C[i][k] Li[j][k], lower triangle i >= j
+        // B[i][j] = sum_{k <= j} C[i][k] Li[j][k] for i >= j, by columns j (from
+        // the last) and rows i (from the last) within a column
         for (int e = b.tid; e < nm * (nm + 1) / 2; e += GP_THREADS) {
-            int i, j;
-            tri_index(e, i, j);
-            const double *Cr = Cm + (size_t)i * ld, *Lj = W.Li + (size_t)j * ld;
+            int r, q;
+            tri_index(e, r, q);
+            const int j = nm - 1 - r, i = nm - 1 - q;
+            const double *Lj = W.Li + (size_t)j * ld;
             double s0 = 0.0, s1 = 0.0;
             int k = 0;
             for (; k + 2 <= j + 1; k += 2) {
-                s0 = fma(Cr[k], Lj[k], s0);
-                s1 = fma(Cr[k + 1], Lj[k + 1], s1);
+                s0 = fma(Ct[(size_t)k * ld + i], Lj[k], s0);
+                s1 = fma(Ct[(size_t)(k + 1) * ld + i], Lj[k + 1], s1);
             }
-            if (k <= j) s0 = fma(Cr[k], Lj[k], s0);
+            if (k <= j) s0 = fma(Ct[(size_t)k * ld + i], Lj[k], s0);
             const double Bij = s0 + s1;
             if (i == j) {
                 trA1 += Bij;
@@ -339,33 +392,48 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
             W.A1[(size_t)i * ld + k] = s0 + s1;
         }
     }
-    // t1 = K' a
+    // t1 = K' a (K' symmetric: read by columns)
     for (int i = b.tid; i < nm; i += GP_THREADS) {
-        double s = 0.0;
-        for (int k = 0; k < nm; k++) s = fma(Kp[(size_t)i * ld + k], a[k], s);
-        t1[i] = s;
+        double s0 = 0.0, s1 = 0.0;
+        int k = 0;
+        for (; k + 2 <= nm; k += 2) {
+            s0 = fma(Kp[(size_t)k * ld + i], a[k], s0);
+            s1 = fma(Kp[(size_t)(k + 1) * ld + i], a[k + 1], s1);
+        }
+        if (k < nm) s0 = fma(Kp[(size_t)k * ld + i], a[k], s0);
+        t1[i] = s0 + s1;
     }
     __syncthreads();
+    // the lower triangle of K'' = (D^2/d^4 - 2D/d^3) o E with its off-diagonal
+    // entries doubled (exact scalings by 2; its diagonal is zero)
+    const double id4x2 = 2.0 * id4, id3x4 = 4.0 * id3;
     double trKiK2 = 0.0, aK2a = 0.0, trKi = 0.0, ata = 0.0;
-    for (int e = b.tid; e < nm * nm; e += GP_THREADS) {
-        int i = e / nm, k = e - i * nm;
-        if (!L_FREE) trA1A1 = fma(W.A1[(size_t)i * ld + k], W.A1[(size_t)k * ld + i], trA1A1);
-        double Dik = W.D[(size_t)i * ld + k];
-        double E = (i == k) ? 0.0 : W.K[(size_t)i * ld + k];
-        double K2 = (Dik * Dik * id4 - 2.0 * Dik * id3) * E;
-        trKiK2 = fma(W.Ki[(size_t)i * ld + k], K2, trKiK2);
-        aK2a = fma(a[i] * K2, a[k], aK2a);
+    for (int e = b.tid; e < nm * (nm + 1) / 2; e += GP_THREADS) {
+        int i, k;
+        tri_index(e, i, k);
         if (i == k) {
             if (!L_FREE) trA1 += W.A1[(size_t)i * ld + i];
+            if (!L_FREE) trA1A1 = fma(W.A1[(size_t)i * ld + i], W.A1[(size_t)i * ld + i], trA1A1);
             trKi += W.Ki[(size_t)i * ld + i];
             ata = fma(a[i], a[i], ata);
+            continue;
         }
+        if (!L_FREE) trA1A1 = fma(2.0 * W.A1[(size_t)i * ld + k], W.A1[(size_t)k * ld + i], trA1A1);
+        const double Dik = W.D[(size_t)i * ld + k];
+        const double K2w = (Dik * Dik * id4x2 - Dik * id3x4) * W.K[(size_t)i * ld + k];
+        trKiK2 = fma(W.Ki[(size_t)i * ld + k], K2w, trKiK2);
+        aK2a = fma(a[i] * K2w, a[k], aK2a);
     }
-    // t2 = K^{-1} t1
+    // t2 = K^{-1} t1 (K^{-1} symmetric: read by columns)
     for (int i = b.tid; i < nm; i += GP_THREADS) {
-        double s = 0.0;
-        for (int k = 0; k < nm; k++) s = fma(W.Ki[(size_t)i * ld + k], t1[k], s);
-        t2[i] = s;
+        double s0 = 0.0, s1 = 0.0;
+        int k = 0;
+        for (; k + 2 <= nm; k += 2) {
+            s0 = fma(W.Ki[(size_t)k * ld + i], t1[k], s0);
+            s1 = fma(W.Ki[(size_t)(k + 1) * ld + i], t1[k + 1], s1);
+        }
+        if (k < nm) s0 = fma(W.Ki[(size_t)k * ld + i], t1[k], s0);
+        t2[i] = s0 + s1;
     }
     __syncthreads();
     double phi_p = 0.0, chi_p = 0.0;
@@ -396,7 +464,7 @@ __device__ Derivs llik_derivs(const GpWork &W, int nm, int ld, double d, const d
 }
 
 struct GpShared {
-    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *rd, *xq, *etab;
+    double *xd, *y, *a, *t1, *t2, *t3, *kx, *dx, *rd, *xq, *etab, *ub;
 };
 
 __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
@@ -413,6 +481,7 @@ __device__ GpShared carve(unsigned char *raw, int nmax, int p) {
     S.rd = S.dx + nmax;  // 1 / diag of the current Cholesky factor
     S.xq = S.rd + nmax;
     S.etab = S.xq + p;  // EXP64_TABLE_SIZE: table of exp64_tang
+    S.ub = S.etab + EXP64_TABLE_SIZE;  // 2 (nmax + 2): the Cholesky's column buffers
     return S;
 }
 
@@ -433,7 +502,6 @@ predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws
     for (int i = threadIdx.x; i < EXP64_TABLE_SIZE; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
-    __shared__ double red[GP_WARPS];
     Blk b{(int)threadIdx.x, (int)threadIdx.x & 31, (int)threadIdx.x >> 5};
     for (;;) {
         if (b.tid == 0) s_loc = atomicAdd(counter, 1);
@@ -451,21 +519,22 @@ predict_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws
             build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
             for (int t = b.tid; t < nm; t += GP_THREADS) S.kx[t] = exp(-sqd(S.xq, S.xd + (size_t)t * p, p) / d);
             __syncthreads();
-            if (!block_cholesky(W.K, W.L, S.rd, nm, ld, &s_chol, b)) {
+            // z = L^{-1} Y_n (t1) and w = L^{-1} k_n(x) (t2) with the factorisation
+            const double *const rhs[2] = {S.y, S.kx};
+            double *const sol[2] = {S.t1, S.t2};
+            if (!block_cholesky<2>(W.K, W.L, S.rd, nm, ld, rhs, sol, S.ub, &s_chol, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                if (b.warp == 0) warp_forward(W.L, ld, S.rd, S.y, S.t1, nm, b.lane);   // z
-                if (b.warp == 1) warp_forward(W.L, ld, S.rd, S.kx, S.t2, nm, b.lane);  // w
-                __syncthreads();
                 double m_p = 0.0, psi_p = 0.0, kk_p = 0.0;
                 for (int i = b.tid; i < nm; i += GP_THREADS) {
                     m_p = fma(S.t2[i], S.t1[i], m_p);
                     psi_p = fma(S.t1[i], S.t1[i], psi_p);
                     kk_p = fma(S.t2[i], S.t2[i], kk_p);
                 }
-                mu = block_sum(m_p, red, b);
-                const double psi = block_sum(psi_p, red, b);
-                const double kk = block_sum(kk_p, red, b);
+                double v[3] = {m_p, psi_p, kk_p};
+                block_sums<3>(v, b);
+                mu = v[0];
+                const double psi = v[1], kk = v[2];
                 sv = psi * ((1.0 + g) - kk) / nm;
                 dfv = nm;
             }
@@ -496,7 +565,6 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
     for (int i = threadIdx.x; i < EXP64_TABLE_SIZE; i += GP_THREADS) S.etab[i] = exp64_table_g[i];  // ordered by the loop's first barrier
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
-    __shared__ double red[GP_WARPS];
     Blk b{(int)threadIdx.x, (int)threadIdx.x & 31, (int)threadIdx.x >> 5};
     for (;;) {
         if (b.tid == 0) s_loc = atomicAdd(counter, 1);
@@ -515,10 +583,10 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
             d = fmin(fmax(d, dmin), dmax);
             build_D(S.xd, nm, p, W.D, ld, b);
             build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
-            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
+            if (!llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                dr = llik_derivs<true>(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
+                dr = llik_derivs<true>(W, nm, ld, d, S.t3, S.a, psi, S.rd, S.t1, S.t2, b);
                 while (it < max_iter) {
                     it++;
                     double delta;
@@ -532,7 +600,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     for (int h = 0; h <= 20; h++) {
                         dn = fmin(fmax(d + delta, dmin), dmax);
                         build_K(W.D, nm, ld, dn, g, W.K, S.etab, b);
-                        if (llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &ln, &psin, b) &&
+                        if (llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &ln, &psin, b) &&
                             (short_newton || ln >= l)) {
                             accepted = true;
                             break;
@@ -542,14 +610,14 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     if (!accepted) {
                         // restore K, L, a at the current d
                         build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
-                        llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b);
+                        llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &l, &psi, b);
                         break;
                     }
                     const double step = fabs(dn - d);
                     d = dn;
                     l = ln;
                     psi = psin;
-                    dr = llik_derivs<true>(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
+                    dr = llik_derivs<true>(W, nm, ld, d, S.t3, S.a, psi, S.rd, S.t1, S.t2, b);
                     if (step < 1e-10 * d) break;
                 }
             }
@@ -598,10 +666,10 @@ grad_kernel(GpArgs a, const double *__restrict__ dv, int *counter, double *ws, G
             build_D(S.xd, nm, p, W.D, ld, b);
             build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
             double l, psi;
-            if (!llik_value(W, nm, ld, S.y, S.a, S.t3, S.rd, red, &s_chol, &l, &psi, b)) {
+            if (!llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
-                Derivs dr = llik_derivs<false>(W, nm, ld, d, S.a, psi, S.rd, S.t1, S.t2, red, b);
+                Derivs dr = llik_derivs<false>(W, nm, ld, d, S.t3, S.a, psi, S.rd, S.t1, S.t2, b);
                 // kx, kx_d = (Dx/d^2) kx ; b = K^{-1} kx (t1) by the two triangular
                 // solves (w = L^{-1} kx in t3, v = 1 + g - w^T w: no explicit
                 // inverse, no cancellation against k^T b), K'a (t2), K'b (t3)
@@ -684,7 +752,7 @@ struct GpLaunch {
 template <typename Kern>
 lagp_status prepare(lagp_ctx *ctx, const GpArgs &a, Kern kern, GpLaunch &L) {
     const int ld = (a.nmax + 31) & ~31;
-    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 8 + (size_t)a.p + EXP64_TABLE_SIZE) * 8 + 64;
+    L.smem = ((size_t)a.nmax * a.p + (size_t)a.nmax * 10 + (size_t)a.p + EXP64_TABLE_SIZE + 4) * 8 + 64;
     if (L.smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "n_max x p too large");
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     int occ = 0;
