@@ -123,8 +123,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "c03ae095d36b71b13db02194efd8bd41c2404a3d1fcbe6bc7fea8bb6dd8c18e8",
-               "dram_bytes_per_location": (4.22e9 + 0.68691e9) / 3040}
+ALC_TRAFFIC = {"sha256": "ea5b35d9b9b5a733aa089959f175ecdf628ff94d0a26e2d9ace9ae7b9073cf42",
+               "dram_bytes_per_location": (4.330874e9 + 0.688441e9) / 3040}
 
 
 def alc_source_hash():

@@ -23,7 +23,7 @@
 
 namespace {
 
-constexpr int GP_THREADS = 256;
+constexpr int GP_THREADS = 128;
 constexpr int GP_WARPS = GP_THREADS / 32;
 
 struct Blk {
@@ -556,7 +556,7 @@ struct MleOut {
     int32_t *iters, *status;
 };
 
-__global__ void __launch_bounds__(GP_THREADS, 3)
+__global__ void __launch_bounds__(GP_THREADS, 6)
 mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *counter, double *ws,
            MleOut o) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
