@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "device_util.cuh"
@@ -932,13 +933,30 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
                        int32_t *idx, int32_t *status) {
     cudaStream_t st = ctx->stream;
     ctx->knn_last_M = M;
-    const int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
-    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 12));
-    int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
     // sample stride: about 8 N' sampled rows per candidate set, 1 (exact) for small designs
     const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(64, N / (8 * (int64_t)Npmax)));
+    const int64_t nsamp = (N + stride - 1) / stride;
+    // candidate capacity: the sampled threshold (the rtarget-th smallest of
+    // every stride-th row, rtarget ~ 1.3 N' / stride + 16) collects about
+    // rtarget stride rows with a spread of about sqrt(rtarget) stride; six of
+    // those spreads above (and 512 rows for the error margins) leave an
+    // overflow, and so an exact retry over the whole design (one CTA's pass
+    // over all N rows: at N = 4M it sets the pass's duration), to about one
+    // query in 1e9.  At least 2 N' + 1024, and no more than the power of two
+    // at or above that (the second sort launch's shared memory, sized by
+    // that power of two, keeps its resident CTAs), nor than the sort holds.
+    int32_t Cmax = std::min(2 * Npmax + 1024, CAND_CAP);
+    if (stride > 1) {
+        int32_t pow2 = 1;
+        while (pow2 < Cmax) pow2 <<= 1;
+        const int64_t rt = std::min<int64_t>((13 * (int64_t)Npmax + 10 * stride - 1) / (10 * stride) + 16, nsamp);
+        const double want = (double)rt * stride + 6.0 * std::sqrt((double)rt) * stride + 512.0;
+        Cmax = (int32_t)std::min<double>(std::max<double>(Cmax, std::ceil(want)), std::min(pow2, CAND_CAP));
+    }
+    char *meta = static_cast<char *>(lagp_ws(ctx, WS_KNN_META, META_HEAD + (size_t)M * 12));
+    int32_t *cand = static_cast<int32_t *>(lagp_ws(ctx, WS_KNN_CAND, (size_t)M * Cmax * 4));
     const int pp = row_stride(p);
-    const int64_t Npad = round_up(N, 32), nsamp = (N + stride - 1) / stride;
+    const int64_t Npad = round_up(N, 32);
     const int64_t nsamp_pad = stride > 1 ? round_up(nsamp, 32) : 0;
     const int pv = (p + 3) & ~3;
     float *Y32 = static_cast<float *>(lagp_ws(ctx, WS_KNN_X32, ((size_t)(Npad + nsamp_pad) * pp + (size_t)Npad * pv) * 4));
