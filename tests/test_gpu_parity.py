@@ -368,6 +368,40 @@ def test_predict_grad_matches_oracle(L, O):
     np.testing.assert_allclose(out["dllik_dd"].cpu().numpy(), ll["dllik"], rtol=1e-6, atol=1e-9)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 129, 200])
+def test_local_gp_design_sizes_match_oracle(L, O, n):
+    """Prediction, the Newton MLE and the adjoint at the extremes of the local
+    design size on nearest-neighbour designs: n = 1..3 (a 1 x 1 factor; for
+    n = 1 the likelihood does not depend on d, so every Newton step is the
+    halving rule), and n above 128, where one thread of the factorisation
+    holds two rows of a column (n + 1 rows with y)."""
+    g, d = 1e-3, 2.0
+    w = W.borehole(seed=15, N=20_000, M=6, n=6, Np=300, g=g)
+    sel = O.knn(w.X, w.Xref, n).astype(np.int32)
+    n_arr = np.full(w.M, n)
+    ref = O.predict(w.X, w.Y, w.Xref, sel, n, d, g)
+    out = L.lagp_predict(dev(w.X), dev(w.Y), dev(w.Xref), dev(sel), n, d, g)
+    assert (out["status"].cpu().numpy() == 0).all()
+    check_pred(out["mean"].cpu().numpy(), out["s2"].cpu().numpy(), ref, w.X, w.Y, w.Xref, sel, n_arr, d, g)
+    d0 = np.full(w.M, d)
+    refm = O.mle(w.X, w.Y, sel, n, d0, g, 1e-3, 20.0, 10)
+    m = L.lagp_mle_step(dev(w.X), dev(w.Y), dev(sel), n, d0, g, 1e-3, 20.0, 10)
+    assert (m["status"].cpu().numpy() == 0).all()
+    assert np.array_equal(m["iters"].cpu().numpy(), refm["iters"])
+    np.testing.assert_allclose(m["d"].cpu().numpy(), refm["d"], rtol=1e-6)
+    np.testing.assert_allclose(m["llik"].cpu().numpy(), refm["llik"], rtol=1e-9)
+    scale = np.abs(refm["llik"]) / refm["d"]
+    np.testing.assert_allclose(m["dllik"].cpu().numpy(), refm["dllik"], rtol=1e-5, atol=1e-7 * scale.max())
+    refg = O.predict_grad(w.X, w.Y, w.Xref, sel, n, d, g)
+    gr = L.lagp_predict_grad(dev(w.X), dev(w.Y), dev(w.Xref), dev(sel), n, d, g)
+    for k in ("dmean_dd", "dmean_dg", "ds2_dd", "ds2_dg", "dllik_dg"):
+        r = refg[k]
+        # floor 1e-9 absolute: at n = 1, dl/dg = -1/(2(1+g)) + 1/(2(1+g)) is
+        # zero up to the rounding of two terms of size 1/2
+        np.testing.assert_allclose(gr[k].cpu().numpy(), r, rtol=1e-6, atol=1e-9 * max(np.abs(r).max(), 1.0),
+                                   err_msg=k)
+
+
 # ------------------------------------------------- whole method, host I/O
 
 def test_agp_host_buffers_match_oracle(L, O):
