@@ -196,14 +196,15 @@ class ClockSampler:
 
 def oracle_sample(w, S, seed=0):
     """Time the FP64 oracle (all host cores, OpenMP over locations) on S
-    seeded reference locations of the workload.  Returns (seconds, cores)."""
+    seeded reference locations of the workload.  Returns (seconds, cores,
+    the sampled location indices, the oracle's outputs for them)."""
     from oracle import oracle as O
     O.build()
     cores = O.set_threads(os.cpu_count() or 1)
     samp = np.random.default_rng(seed).choice(w.M, S, replace=False)
     t0 = time.perf_counter()
-    O.run_pipeline(w.X, w.Y, w.Xref[samp], w.n0, w.n[samp], int(w.Np[0]), w.d, w.g)
-    return time.perf_counter() - t0, cores
+    ref = O.run_pipeline(w.X, w.Y, w.Xref[samp], w.n0, w.n[samp], int(w.Np[0]), w.d, w.g)
+    return time.perf_counter() - t0, cores, samp, ref
 
 
 def run_reference(args, rank, world):
@@ -212,10 +213,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(w, 16, seed=99)
+        oracle_sample(w, 16, seed=99)[:2]
     times, cores = [], 1
     for k in range(args.steps):
-        t, cores = oracle_sample(w, S, seed=k)
+        t, cores = oracle_sample(w, S, seed=k)[:2]
         times.append(t)
     sec = sum(times)
     value = S * args.steps / sec
@@ -602,13 +603,44 @@ def run_ours(args, rank, world, local_rank):
         a64 = f64s["fp64_flops_per_launch"] / (f64s["alc_kernel_ms"] / 1e3) / 1e12
         f64s["roofline"] = {"bound": "alu", "kernel": "alc_bulk_kernel (FP64 state)", "unit": "TFLOP/s",
                             "achieved": a64, "peak": fp64_peak, "frac": a64 / fp64_peak}
-    cpu = None
+    cpu, vs_oracle = None, None
     if not args.no_cpu and world == 1:
         S = 1024
-        sec, cores = oracle_sample(w, S)
+        sec, cores, samp, ref = oracle_sample(w, S)
         cpu = {"value": S / sec, "unit": "predictions/s", "cores": cores, "kind": "oracle",
                "sample": f"{S} seeded reference locations of the same workload (FP64 C oracle, "
                          f"OpenMP over locations), {sec:.1f} s"}
+        # the timed run's outputs on the same sample against the oracle's:
+        # kNN sets, greedy designs, and mean / s2 where the designs agree (a
+        # near tie may legitimately send a design another way)
+        idx_g = L.lagp_knn(X, Xr, Np)[0].cpu().numpy()[samp]
+        sel_g = s["sel"].cpu().numpy()[samp][:, :n]
+        same = (sel_g == ref["sel"][:, :n]).all(axis=1)
+
+        def max_rel(a, b):
+            return float(np.max(np.abs(a - b) / np.abs(b))) if len(b) else None
+
+        # the parity bar of the tests: relative 1e-6, or 16 eps cond(K_n)
+        # times the quantity's scale (|Y| for the mean, psi / n for s2), the
+        # forward-error bound of the local FP64 solve, whichever is larger
+        mg, s2g = mean[samp][same], p["s2"].cpu().numpy()[samp][same]
+        bar_m, bar_s = [], []
+        for r in np.flatnonzero(same):
+            rows = ref["sel"][r, :n]
+            A, y = np.asarray(w.X[rows], np.float64), np.asarray(w.Y[rows], np.float64)
+            K = np.exp(-((A[:, None] - A[None]) ** 2).sum(-1) / d) + g * np.eye(n)
+            c = np.linalg.cond(K)
+            psi = y @ np.linalg.solve(K, y)
+            bar_m.append(max(1e-6 * abs(ref["mean"][r]), 16 * np.finfo(float).eps * c * np.abs(y).max()))
+            bar_s.append(max(1e-6 * abs(ref["s2"][r]), 16 * np.finfo(float).eps * c * psi / n))
+        vs_oracle = {"sample": S, "knn_identical_frac": float((idx_g == ref["idx"]).all(axis=1).mean()),
+                     "identical_designs_frac": float(same.mean()),
+                     "max_rel_err_mean": max_rel(mg, ref["mean"][same]),
+                     "max_rel_err_s2": max_rel(s2g, ref["s2"][same]),
+                     "max_err_over_parity_bar_mean":
+                         float(np.max(np.abs(mg - ref["mean"][same]) / np.array(bar_m))) if bar_m else None,
+                     "max_err_over_parity_bar_s2":
+                         float(np.max(np.abs(s2g - ref["s2"][same]) / np.array(bar_s))) if bar_s else None}
     line = {
         "metric": METRIC, "value": value, "unit": "predictions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -625,7 +657,7 @@ def run_ours(args, rank, world, local_rank):
         "cuda_graph": graph_ms,
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+        "roofline": roofline, "cpu_baseline": cpu, "vs_oracle": vs_oracle, "clocks": clocks,
         "configs": configs,
         "alc_eval_one_location": e1,
     }
