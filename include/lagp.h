@@ -161,10 +161,11 @@ lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, la
  *           FP64 in coordinate order without fused multiply-add; entries past
  *           Nprime[m] are -1.  The result is bit-exact and deterministic.
  *   status  M int32 output or NULL: LAGP_OK; LAGP_EINVAL (Nprime[m] outside
- *           [1, Nprime_max], or non-finite distances); LAGP_ENOMEM (more than
- *           min(2 Nprime_max + 1024, 8192) design rows lie within FP32
- *           screening resolution of the N'-th distance, i.e. massively
- *           duplicated rows).  A failed location's idx row is -1.
+ *           [1, Nprime_max], or non-finite distances); LAGP_ENOMEM (more
+ *           design rows than the candidate capacity, at least
+ *           min(2 Nprime_max + 1024, 8192), lie within FP32 screening
+ *           resolution of the N'-th distance, i.e. massively duplicated
+ *           rows).  A failed location's idx row is -1.
  * Requires 1 <= Nprime_max <= min(N, 4096), N < 2^31 and 1 <= p <= 64. */
 lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
                      const void *Xref, int64_t M, const int32_t *Nprime, int32_t Nprime_max,
