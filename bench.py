@@ -76,17 +76,17 @@ def workload_for_rank(rank: int, M=None):
 
 
 def work_per_location(n0, n, Np):
-    """Algorithmic counts per location: ALC candidate evaluations of the
-    greedy search, E = sum_{j=n0}^{n-1} (N' - j), and the FP32 flops of the
-    bulk screen's Schur recurrence: after step j every unchosen candidate
-    takes a dot product of length j with the pivot column (2j), its squared
-    distance to the new design point (3p), and the updates of u, v, r and the
-    score (8)."""
+    """ALC candidate evaluations of one location's greedy search,
+    E = sum_{j=n0}^{n-1} (N' - j)."""
     E = sum(Np - j for j in range(n0, n))
     return E
 
 
 def fp32_flops_per_location(n, Np, p):
+    """FP32 flops of the bulk screen's Schur recurrence for one location:
+    after step j every unchosen candidate takes a dot product of length j
+    with the pivot column (2j), its squared distance to the new design point
+    (3p), and the updates of u, v, r and the score (8)."""
     return sum((Np - j - 1) * (2 * j + 3 * p + 8) for j in range(0, n - 1))
 
 
