@@ -194,13 +194,14 @@ class ClockSampler:
 
 # ------------------------------------------------------------- oracle legs
 
-def oracle_sample(w, S, seed=0):
-    """Time the FP64 oracle (all host cores, OpenMP over locations) on S
-    seeded reference locations of the workload.  Returns (seconds, cores,
-    the sampled location indices, the oracle's outputs for them)."""
+def oracle_sample(w, S, seed=0, threads=None):
+    """Time the FP64 oracle (all host cores unless `threads`, OpenMP over
+    locations) on S seeded reference locations of the workload.  Returns
+    (seconds, cores, the sampled location indices, the oracle's outputs for
+    them)."""
     from oracle import oracle as O
     O.build()
-    cores = O.set_threads(os.cpu_count() or 1)
+    cores = O.set_threads(threads or os.cpu_count() or 1)
     samp = np.random.default_rng(seed).choice(w.M, S, replace=False)
     t0 = time.perf_counter()
     ref = O.run_pipeline(w.X, w.Y, w.Xref[samp], w.n0, w.n[samp], int(w.Np[0]), w.d, w.g)
@@ -610,6 +611,10 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": S / sec, "unit": "predictions/s", "cores": cores, "kind": "oracle",
                "sample": f"{S} seeded reference locations of the same workload (FP64 C oracle, "
                          f"OpenMP over locations), {sec:.1f} s"}
+        S1 = 64
+        sec1, _, _, _ = oracle_sample(w, S1, seed=1, threads=1)
+        cpu["single_core"] = {"value": S1 / sec1, "unit": "predictions/s", "cores": 1,
+                              "sample": f"{S1} seeded reference locations, one thread, {sec1:.1f} s"}
         # the timed run's outputs on the same sample against the oracle's:
         # kNN sets, greedy designs, and mean / s2 where the designs agree (a
         # near tie may legitimately send a design another way)
