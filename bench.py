@@ -130,7 +130,7 @@ ALC_TRAFFIC = {"sha256": "ea5b35d9b9b5a733aa089959f175ecdf628ff94d0a26e2d9ace9ae
 def alc_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("alc_f32.cu", "exp64.cuh", "device_util.cuh", "lagp_internal.h"):
+    for f in ("alc_bulk32.cu", "alc_common.cuh", "df64.cuh", "exp64.cuh", "device_util.cuh", "lagp_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1310_5182_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

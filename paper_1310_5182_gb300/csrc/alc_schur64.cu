@@ -1,7 +1,8 @@
-// a2..a6 in the Schur-complement (incremental) form: greedy ALC local design
-// search (Fig. 1 step 2 of the paper) with the bulk candidate state in FP32
-// (the FP32-bulk form) or in FP64 (the FP64 Schur form), and every decision
-// in FP64.
+// a2..a6 in the Schur-complement (incremental) form with the candidate state
+// in FP64 -- the FP64 Schur form of the greedy ALC local design search
+// (Fig. 1 step 2 of the paper) -- and every decision in FP64.  (The same form
+// with the candidate state in FP32 and the decisions in double-float is
+// alc_bulk32.cu.)
 //
 // Why not K_j^{-1} in FP32: the local matrices of these workloads are
 // ill-conditioned (cond(K_j) ~ 1e5..1e7 for nuggets 1e-4..1e-6), so the FP32
@@ -20,14 +21,14 @@
 // direct form is O(j^2)); in FP32 its rounding error is ~j 2^-24 absolute,
 // in FP64 ~j 2^-53.
 //
-// Each step: FP32 scores r^2 / v of the bulk state -> contenders (scores
-// within an adaptive margin of the maximum, at most rescore_max) -> FP64
-// re-score of the contenders with the three-term Eq. (dxy) against FP64
-// K_j^{-1} -> argmax (ties to the lower row) -> FP64 partitioned-inverse
-// update of K_j^{-1} (Sec. 2.2) -> the bulk recurrence with pivot x*, whose
-// lambda and r_{x*} come from the pivot's own bulk state (self-consistent
-// factor).  With FP64 state the scores differ from FP64 only by their FP32
-// rounding, so the margin floor is 1e-5 and one contender is the rule.
+// Each step: FP32 roundings of the FP64 scores r^2 / v -> contenders (scores
+// within a margin of the maximum, at most rescore_max; the FP32 rounding
+// alone separates them from the exact scores, so the margin floor is 1e-5
+// and one contender is the rule) -> FP64 re-score of the contenders with the
+// three-term Eq. (dxy) against FP64 K_j^{-1} -> argmax (ties to the lower
+// row) -> FP64 partitioned-inverse update of K_j^{-1} (Sec. 2.2) -> the bulk
+// recurrence with pivot x*, whose lambda and r_{x*} come from the pivot's own
+// bulk state (self-consistent factor).
 //
 // Layout: one persistent CTA per location at a time (atomic work counter),
 // several CTAs per SM so that one location's serial FP64 phases overlap
@@ -42,6 +43,7 @@
 
 #include <algorithm>
 
+#include "alc_common.cuh"
 #include "device_util.cuh"
 #include "exp64.cuh"
 #include "lagp_internal.h"
@@ -50,12 +52,11 @@ namespace {
 
 constexpr int F32_THREADS = 256;
 constexpr int F32_WARPS = F32_THREADS / 32;
-// Adaptive contender margin: FP32 scores within `margin` (relative) of the
-// FP32 maximum are re-scored in FP64, margin = min(rescore_rel,
-// max(MARGIN_MIN, MARGIN_KAPPA * err)), where err is the largest relative
-// FP32-vs-FP64 score error seen among the contenders re-scored so far,
-// decaying by ERR_DECAY per step (starting at ERR_INIT).
-constexpr float MARGIN_MIN = 0.02f;
+// Contender margin: FP32 scores within `margin` (relative) of the FP32
+// maximum are re-scored in FP64, margin = min(rescore_rel,
+// max(MARGIN_MIN_F64STATE, MARGIN_KAPPA * err)), where err is the largest
+// relative FP32-vs-FP64 score error seen among the contenders re-scored so
+// far, decaying by ERR_DECAY per step (starting at ERR_INIT).
 // with FP64 state the FP32 scores only round (the state is exact to FP64
 // rounding), so the margin's floor is a few FP32 ulps
 constexpr float MARGIN_MIN_F64STATE = 1e-5f;
@@ -63,68 +64,15 @@ constexpr float MARGIN_KAPPA = 8.0f;
 constexpr float ERR_DECAY = 0.75f;
 constexpr float ERR_INIT = 0.05f;
 
-template <typename T>
-struct Vec2;
-template <>
-struct Vec2<float> {
-    using type = float2;
-};
-template <>
-struct Vec2<double> {
-    using type = double2;
-};
+using alc::load_vec;
+using alc::store_vec;
+using alc::order_key;
+using alc::warp_best3;
 
-// CPT consecutive values of a candidate-indexed row (vector loads/stores)
-template <int CPT, typename T>
-__device__ __forceinline__ void load_vec(const T *p, T (&v)[CPT]) {
-    if constexpr (sizeof(T) == 4 && CPT % 4 == 0) {
-#pragma unroll
-        for (int r = 0; r < CPT; r += 4) {
-            float4 t = *reinterpret_cast<const float4 *>(p + r);
-            v[r] = t.x;
-            v[r + 1] = t.y;
-            v[r + 2] = t.z;
-            v[r + 3] = t.w;
-        }
-    } else if constexpr (CPT % 2 == 0) {
-#pragma unroll
-        for (int r = 0; r < CPT; r += 2) {
-            typename Vec2<T>::type t = *reinterpret_cast<const typename Vec2<T>::type *>(p + r);
-            v[r] = t.x;
-            v[r + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < CPT; r++) v[r] = p[r];
-    }
-}
-
-template <int CPT, typename T>
-__device__ __forceinline__ void store_vec(T *p, const T (&v)[CPT]) {
-    if constexpr (sizeof(T) == 4 && CPT % 4 == 0) {
-#pragma unroll
-        for (int r = 0; r < CPT; r += 4)
-            *reinterpret_cast<float4 *>(p + r) = make_float4(v[r], v[r + 1], v[r + 2], v[r + 3]);
-    } else if constexpr (CPT % 2 == 0) {
-#pragma unroll
-        for (int r = 0; r < CPT; r += 2) {
-            typename Vec2<T>::type t;
-            t.x = v[r];
-            t.y = v[r + 1];
-            *reinterpret_cast<typename Vec2<T>::type *>(p + r) = t;
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < CPT; r++) p[r] = v[r];
-    }
-}
-
-// K = exp(a) for the bulk state: FP32 (fast intrinsic) or FP64 (table method)
-__device__ __forceinline__ float bulk_exp(float a, const double *) { return __expf(a); }
+// K = exp(a) for the bulk state (table method)
 __device__ __forceinline__ double bulk_exp(double a, const double *etab) { return exp64_tang(a, etab); }
 
-// FP32 screening score r^2 / v from the bulk state
-__device__ __forceinline__ float bulk_score(float cov, float v, float gf) { return cov * cov / fmaxf(v, gf); }
+// FP32 screening score r^2 / v of the FP64 bulk state
 __device__ __forceinline__ float bulk_score(double cov, double v, float gf) {
     const float c = (float)cov;
     return c * c / fmaxf((float)v, gf);
@@ -179,41 +127,17 @@ __device__ __forceinline__ void partial_contract(const double *kc, const double 
         if (lane + 32 * r < jo) out[lane + 32 * r] = b0[r] + b1[r];
 }
 
-// Integer key with the order of the doubles (for comparisons off the FP64 pipe)
-__device__ __forceinline__ long long order_key(double x) {
-    const long long b = __double_as_longlong(x);
-    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-
-// (score, row, slot) argmax across a warp: larger score, ties to the lower row
-__device__ __forceinline__ void warp_best3(float &s, int &row, int &slot) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float os = __shfl_xor_sync(LAGP_FULL_MASK, s, o);
-        int orow = __shfl_xor_sync(LAGP_FULL_MASK, row, o);
-        int oslot = __shfl_xor_sync(LAGP_FULL_MASK, slot, o);
-        if (os > s || (os == s && orow < row)) {
-            s = os;
-            row = orow;
-            slot = oslot;
-        }
-    }
-}
-
-// four resident CTAs per SM (64 registers a thread) for up to 4 candidate
-// slots a thread, fewer for the wider variants whose state needs more
-// T: the type of the bulk state (U, v, r and the candidate coordinates):
-// float for the FP32-bulk form, double for the FP64 Schur form.  Scores,
-// contenders, the re-score and the update are the same for both.
+// resident CTAs per SM: two for up to 4 candidate slots a thread, one for
+// the wider variants.  T is the type of the bulk state (U, v, r and the
+// candidate coordinates): double.
 template <typename T, int CPT>
 constexpr int bulk_min_blocks() {
-    return sizeof(T) == 8 ? (CPT >= 8 ? 1 : 2) : (CPT >= 16 ? 2 : (CPT >= 8 ? 3 : 4));
+    return CPT >= 8 ? 1 : 2;
 }
 
 template <int CPT, typename T>
 __global__ void __launch_bounds__(F32_THREADS, bulk_min_blocks<T, CPT>())
 alc_bulk_kernel(F32Params P) {
-    constexpr bool F64STATE = sizeof(T) == 8;
     const AlcArgs &a = P.a;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, Npmax = a.Npmax, Npad = P.Npad, tmax = P.tmax;
@@ -306,8 +230,7 @@ alc_bulk_kernel(F32Params P) {
         for (int i = tid; i < p; i += F32_THREADS) xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
         for (int e = tid; e < p * Npad; e += F32_THREADS) {
             int i = e / Npad, c = e - i * Npad;
-            if constexpr (F64STATE) Cg[e] = c < k ? load_coord64(a.X, cands[c], p, i, a.dtype) : 0.0;
-            else Cg[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
+            Cg[e] = c < k ? load_coord64(a.X, cands[c], p, i, a.dtype) : 0.0;
         }
         const double inv_d64 = 1.0 / d, onepg = 1.0 + g;
         if (tid == 0) {
@@ -320,7 +243,7 @@ alc_bulk_kernel(F32Params P) {
         __syncthreads();
         const T inv_d = (T)(1.0 / d);
         const float gf = fmaxf((float)g, FLT_MIN);  // floor of v in the FP32 scores
-        const T gT = F64STATE ? (T)fmax(g, DBL_MIN) : (T)gf;
+        const T gT = (T)fmax(g, DBL_MIN);
         T v[CPT], cov[CPT];
         float score[CPT];
         int rows[CPT];  // design rows of this thread's candidates (tie-break key)
@@ -374,7 +297,7 @@ alc_bulk_kernel(F32Params P) {
                 }
             } else {
                 const float margin =
-                    fminf(P.rel, fmaxf(F64STATE ? MARGIN_MIN_F64STATE : MARGIN_MIN, MARGIN_KAPPA * s_err));
+                    fminf(P.rel, fmaxf(MARGIN_MIN_F64STATE, MARGIN_KAPPA * s_err));
                 float gmax = w_max[0];
 #pragma unroll
                 for (int w = 1; w < F32_WARPS; w++) gmax = fmaxf(gmax, w_max[w]);
@@ -666,9 +589,7 @@ alc_bulk_kernel(F32Params P) {
             for (int r = 0; r < CPT; r++)
                 if (c0 + r == cstar) {
                     const T vs = v[r] > gT ? v[r] : gT;
-                    T il;
-                    if constexpr (F64STATE) il = 1.0 / sqrt(vs);
-                    else il = rsqrtf(vs);
+                    const T il = 1.0 / sqrt(vs);
                     s_invlam = il;
                     s_wnew = cov[r] * il;
                     chosen |= 1u << r;
@@ -684,7 +605,7 @@ alc_bulk_kernel(F32Params P) {
                 for (int r = 0; r < CPT; r++) acc[r] = T(0);
                 const T *Ub = U + c0;
                 // loads in flight per thread: UNR rows of CPT values
-                constexpr int UNR = (F64STATE || CPT >= 16) ? 2 : 6;
+                constexpr int UNR = 2;
                 int i = 0;
                 for (; i + UNR <= j; i += UNR) {
                     T u[UNR][CPT];
@@ -823,7 +744,5 @@ lagp_status launch_bulk(lagp_ctx *ctx, const AlcArgs &a) {
 }
 
 }  // namespace
-
-lagp_status launch_alc_f32(lagp_ctx *ctx, const AlcArgs &a) { return launch_bulk<float>(ctx, a); }
 
 lagp_status launch_alc_f64schur(lagp_ctx *ctx, const AlcArgs &a) { return launch_bulk<double>(ctx, a); }
