@@ -50,9 +50,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay leg")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations (2-d toy in both precisions, the 1M-point "
-                         "uneven borehole with MLE)")
-    ap.add_argument("--extra", action="store_true",
-                    help="also time the 3-d slab grid and the 4M-point borehole (both with MLE)")
+                         "uneven borehole, the 3-d slab grid and the 4M-point borehole, all with MLE)")
     ap.add_argument("--config", default=None, choices=sorted(W.CONFIGS),
                     help="time only this configuration's leg and print it as one JSON line "
                          "(per-configuration timing and profiler captures; not the headline)")
@@ -237,10 +235,63 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------- the other configurations
 
-def config_leg(L, dev, w, prec, steps, warmup, flush=None):
+def parity_bars(X, Y, sel, n_arr, d, g, ref_mean, ref_s2):
+    """The tests' parity bar per location: relative 1e-6, or 16 eps cond(K_n)
+    times the quantity's scale (|Y| for the mean, psi / n for s2), the
+    forward-error bound of the local FP64 solve, whichever is larger."""
+    eps = np.finfo(float).eps
+    bm, bs = np.empty(len(sel)), np.empty(len(sel))
+    for r in range(len(sel)):
+        n = int(n_arr[r])
+        rows = sel[r, :n]
+        A, y = np.asarray(X[rows], np.float64), np.asarray(Y[rows], np.float64)
+        K = np.exp(-((A[:, None] - A[None]) ** 2).sum(-1) / d[r]) + g * np.eye(n)
+        c = np.linalg.cond(K)
+        psi = y @ np.linalg.solve(K, y)
+        bm[r] = max(1e-6 * abs(ref_mean[r]), 16 * eps * c * np.abs(y).max())
+        bs[r] = max(1e-6 * abs(ref_s2[r]), 16 * eps * c * psi / n)
+    return bm, bs
+
+
+def vs_oracle_leg(w, out, S, seed=7):
+    """The GPU run's outputs against the FP64 oracle on S seeded locations:
+    kNN sets, greedy designs, d-hat (with the MLE) and, where the designs
+    agree (a near tie may send a design another way), mean and s2 against
+    the tests' parity bar.  Returns (dict, oracle seconds, cores)."""
+    from oracle import oracle as O
+    O.build()
+    cores = O.set_threads(os.cpu_count() or 1)
+    S = min(S, w.M)
+    samp = np.sort(np.random.default_rng(seed).choice(w.M, S, replace=False))
+    t0 = time.perf_counter()
+    ref = O.run_pipeline(w.X, w.Y, w.Xref[samp], w.n0, w.n[samp], int(w.Np.max()), w.d, w.g,
+                         mle_args=w.mle, Np_arr=w.Np[samp])
+    sec = time.perf_counter() - t0
+    nmax = int(w.n.max())
+    sel_g = out["sel"][samp][:, :nmax]
+    same = np.array([(sel_g[r, :w.n[i]] == ref["sel"][r, :w.n[i]]).all() for r, i in enumerate(samp)])
+    d_ref = np.broadcast_to(np.asarray(ref["d"], np.float64), (S,))
+    res = {"sample": S, "oracle_s": round(sec, 2),
+           "knn_identical_frac": float((out["idx"][samp][:, :ref["idx"].shape[1]] == ref["idx"]).all(axis=1).mean()),
+           "identical_designs_frac": float(same.mean())}
+    if w.mle is not None:
+        d_g = out["d"][samp]
+        res["max_rel_err_d"] = float(np.max(np.abs(d_g[same] - d_ref[same]) / d_ref[same])) if same.any() else None
+    if same.any():
+        r = np.flatnonzero(same)
+        bm, bs = parity_bars(w.X, w.Y, ref["sel"][r], w.n[samp][r], d_ref[r], w.g, ref["mean"][r], ref["s2"][r])
+        res["max_err_over_parity_bar_mean"] = float(np.max(np.abs(out["mean"][samp][r] - ref["mean"][r]) / bm))
+        res["max_err_over_parity_bar_s2"] = float(np.max(np.abs(out["s2"][samp][r] - ref["s2"][r]) / bs))
+        res["max_rel_err_mean"] = float(np.max(np.abs(out["mean"][samp][r] - ref["mean"][r]) /
+                                               np.abs(ref["mean"][r])))
+    return res, sec, cores
+
+
+def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
     """Whole-batch rate of one configuration: kNN, then either the fused
     search + prediction (fixed d) or search -> Newton MLE of d -> prediction
-    (w.mle set), with per-location n and N' as device arrays."""
+    (w.mle set), with per-location n and N' as device arrays; the last step's
+    outputs against the oracle on a seeded subsample of oracle_S locations."""
     import torch
     X, Y, Xr = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.X, w.Y, w.Xref))
     n_t = torch.from_numpy(w.n).to(dev)
@@ -253,11 +304,12 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None):
         if w.mle is None:
             out = L.lagp_alc_predict(X, Y, Xr, idx, w.n0, n_t, w.d, w.g, prec=prec, Nprime=Np_t,
                                      n_max=nmax)
-            return out["mean"], [st, out["status"]]
+            return dict(idx=idx, sel=out["sel"], mean=out["mean"], s2=out["s2"]), [st, out["status"]]
         s = L.lagp_alc_select(X, Xr, idx, w.n0, n_t, w.d, w.g, prec=prec, Nprime=Np_t, n_max=nmax)
         m = L.lagp_mle_step(X, Y, s["sel"], n_t, w.d, w.g, *w.mle)
         pr = L.lagp_predict(X, Y, Xr, s["sel"], n_t, m["d"], w.g)
-        return pr["mean"], [st, s["status"], m["status"], pr["status"]]
+        return (dict(idx=idx, sel=s["sel"], d=m["d"], mean=pr["mean"], s2=pr["s2"]),
+                [st, s["status"], m["status"], pr["status"]])
 
     for _ in range(warmup):
         step()
@@ -268,18 +320,22 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None):
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mean, sts = step()
+        outs, sts = step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         times.append(e0.elapsed_time(e1))
     ok = np.all([t.cpu().numpy() == 0 for t in sts], axis=0)
-    mean = mean.cpu().numpy()
+    outs = {k: v.cpu().numpy() for k, v in outs.items()}
+    mean = outs["mean"]
     ms = statistics.mean(times)
-    return {"value": w.M / (ms / 1e3), "unit": "predictions/s", "ms_per_step": ms, "steps": steps,
-            "M": w.M, "N": w.N, "p": w.p, "n": [int(w.n.min()), int(w.n.max())],
-            "Nprime": [int(w.Np.min()), int(w.Np.max())], "dtype": str(w.X.dtype), "prec": prec,
-            "mle": list(w.mle) if w.mle else None, "status_ok_frac": float(ok.mean()),
-            "rmse_vs_truth": float(np.sqrt(np.mean((mean[ok] - w.truth[ok]) ** 2)))}
+    res = {"value": w.M / (ms / 1e3), "unit": "predictions/s", "ms_per_step": round(ms, 3), "steps": steps,
+           "M": w.M, "N": w.N, "p": w.p, "n": [int(w.n.min()), int(w.n.max())],
+           "Nprime": [int(w.Np.min()), int(w.Np.max())], "dtype": str(w.X.dtype), "prec": prec,
+           "mle": list(w.mle) if w.mle else None, "status_ok_frac": float(ok.mean()),
+           "rmse_vs_truth": float(np.sqrt(np.mean((mean[ok] - w.truth[ok]) ** 2)))}
+    if oracle_S:
+        res["vs_oracle"] = vs_oracle_leg(w, outs, oracle_S)[0]
+    return res
 
 
 def alc_eval_sweep(L, dev, flush, ns=range(16, 513, 4), Nc=60_000, oracle_ns=(16, 64, 128, 256),
@@ -349,22 +405,32 @@ def alc_eval_sweep(L, dev, flush, ns=range(16, 513, 4), Nc=60_000, oracle_ns=(16
 
 
 def other_configs(L, dev, args, flush):
+    """BASELINE's other configurations on this GPU, each against the FP64
+    oracle on a seeded subsample (the 2-d toy: all 100 locations; the others:
+    1,000), and the 4M-point borehole also end to end through the host-buffer
+    call (its wall time, copies included)."""
     out = {}
     w1 = W.c1_toy2d_fp64()
     for prec in ("f64", "f32bulk"):
-        out[f"toy2d_N10000_M100_n50_Nprime1000_{prec}"] = config_leg(L, dev, w1, prec, 10, 3, flush)
-    w3 = W.c3_borehole_1m_uneven()
-    out["borehole8d_N1000000_M20000_n30-100_Nprime500-2000_mle"] = config_leg(L, dev, w3, "f32bulk", 2, 1,
-                                                                              flush)
-    del w3
-    if args.extra:
-        w4 = W.c4_slab3d()
-        out["slab3d_N500000_grid60x60x56_n60_Nprime1500_mle"] = config_leg(L, dev, w4, "f32bulk", 2, 1,
-                                                                           flush)
-        del w4
-        w5 = W.c5_borehole_4m()
-        out["borehole8d_N4000000_M100000_n50_Nprime2000_mle"] = config_leg(L, dev, w5, "f32bulk", 2, 1,
-                                                                           flush)
+        out[f"toy2d_N10000_M100_n50_Nprime1000_{prec}"] = config_leg(L, dev, w1, prec, 10, 3, flush, oracle_S=100)
+    legs = [("borehole8d_N1000000_M20000_n30-100_Nprime500-2000_mle", W.c3_borehole_1m_uneven, 2, 1),
+            ("slab3d_N500000_grid60x60x56_n60_Nprime1500_mle", W.c4_slab3d, 1, 1),
+            ("borehole8d_N4000000_M100000_n50_Nprime2000_mle", W.c5_borehole_4m, 1, 1)]
+    for name, make, steps, warm in legs:
+        w = make()
+        out[name] = config_leg(L, dev, w, "f32bulk", steps, warm, flush, oracle_S=1000)
+        if make is W.c5_borehole_4m:
+            # end to end through the public host-buffer call: kNN, search, MLE,
+            # predict, with the copies in both directions inside
+            import torch
+            t0 = time.perf_counter()
+            r = L.lagp_agp(w.X, w.Y, w.Xref, w.n0, int(w.n[0]), int(w.Np[0]), w.d, w.g, prec="f32bulk",
+                           mle=w.mle, device=dev.index or 0)
+            wall = time.perf_counter() - t0
+            out[name]["e2e_wall_s"] = round(wall, 3)
+            out[name]["e2e_value"] = w.M / wall
+            out[name]["e2e_status_ok_frac"] = float((r["status"] == 0).mean())
+        del w
     return out
 
 
@@ -570,36 +636,32 @@ def run_ours(args, rank, world, local_rank):
     e1 = None
     if not args.no_configs and world == 1:
         configs = other_configs(L, dev, args, flush)
-        e1 = alc_eval_sweep(L, dev, flush, cpu=not args.no_cpu)
+        e1 = alc_eval_sweep(L, dev, flush, ns=(16, 32, 64, 128, 256, 384, 512), cpu=not args.no_cpu)
     if rank != 0:
         return
     E = work_per_location(n0, n, Np)
     alc_avg = statistics.mean(alc_ms) / 1e3
-    # peaks: the dominant kernel is bound by the FP64 unit (the re-score and
-    # the update of K^{-1}); FP64 and FP32 peaks from the unit counts and the
-    # SM clock sampled during the timed region
+    # peaks from the unit counts and the SM clock sampled during the timed
+    # region: FP32 (the FP32-bulk kernel issues no FP64 instruction) and FP64
+    # (the FP64 forms)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
     fp64_peak = sms * 4 * mhz * 1e6 / 1e12      # 2 FP64 FMA lanes / cycle / SM
     fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12  # 128 FP32 FMA lanes / cycle / SM
-    per_launch = {k: v / args.steps for k, v in work.items()}
-    fl64 = fp64_flops(per_launch, M, n, w.p, True)
-    if args.prec == "f64schur":  # the bulk pass is FP64 work too
-        fl64 += M * fp64_schur_pass_flops_per_location(n, Np, w.p)
     fl32 = M * fp32_flops_per_location(n, Np, w.p)
-    achieved = fl64 / alc_avg / 1e12
     traffic = None
     if ALC_TRAFFIC["sha256"] == alc_source_hash() and ALC_TRAFFIC["dram_bytes_per_location"]:
         traffic = ALC_TRAFFIC["dram_bytes_per_location"] * M
-    roofline = {"bound": "alu", "kernel": "alc_bulk_kernel<4, float>", "unit": "TFLOP/s", "achieved": achieved,
-                "peak": fp64_peak, "frac": achieved / fp64_peak, "traffic": traffic,
-                "peak_source": f"derived: FP64, {sms} SMs x 4 flop/cycle x {mhz:.0f} MHz (sampled)",
-                "fp64_flops_per_launch": fl64,
-                "rescored_per_step": work["rescored"] / max(1, work["locations"]) / n,
-                "fp32_screen": {"achieved": fl32 / alc_avg / 1e12, "peak": fp32_peak,
-                                "frac": fl32 / alc_avg / 1e12 / fp32_peak, "unit": "TFLOP/s",
-                                "flops_per_launch": fl32}}
+    cpt = 8 if Np > 512 else (4 if Np > 256 else 2)
+    # the FP32 flops of the bulk screen's Schur recurrence (the work the
+    # kernel does per candidate and step; the double-float re-score of the
+    # ~1.4 contenders a step is not counted)
+    roofline = {"bound": "alu", "kernel": f"alc_bulk32_kernel<{cpt}>", "unit": "TFLOP/s",
+                "achieved": fl32 / alc_avg / 1e12, "peak": fp32_peak, "frac": fl32 / alc_avg / 1e12 / fp32_peak,
+                "traffic": traffic, "flops_per_launch": fl32,
+                "peak_source": f"derived: FP32 FMA, {sms} SMs x 256 flop/cycle x {mhz:.0f} MHz (sampled)",
+                "rescored_per_step": work["rescored"] / max(1, work["locations"]) / n}
     if f64s is not None:
         a64 = f64s["fp64_flops_per_launch"] / (f64s["alc_kernel_ms"] / 1e3) / 1e12
         f64s["roofline"] = {"bound": "alu", "kernel": "alc_bulk_kernel (FP64 state)", "unit": "TFLOP/s",
@@ -621,31 +683,19 @@ def run_ours(args, rank, world, local_rank):
         idx_g = L.lagp_knn(X, Xr, Np)[0].cpu().numpy()[samp]
         sel_g = s["sel"].cpu().numpy()[samp][:, :n]
         same = (sel_g == ref["sel"][:, :n]).all(axis=1)
-
-        def max_rel(a, b):
-            return float(np.max(np.abs(a - b) / np.abs(b))) if len(b) else None
-
-        # the parity bar of the tests: relative 1e-6, or 16 eps cond(K_n)
-        # times the quantity's scale (|Y| for the mean, psi / n for s2), the
-        # forward-error bound of the local FP64 solve, whichever is larger
         mg, s2g = mean[samp][same], p["s2"].cpu().numpy()[samp][same]
-        bar_m, bar_s = [], []
-        for r in np.flatnonzero(same):
-            rows = ref["sel"][r, :n]
-            A, y = np.asarray(w.X[rows], np.float64), np.asarray(w.Y[rows], np.float64)
-            K = np.exp(-((A[:, None] - A[None]) ** 2).sum(-1) / d) + g * np.eye(n)
-            c = np.linalg.cond(K)
-            psi = y @ np.linalg.solve(K, y)
-            bar_m.append(max(1e-6 * abs(ref["mean"][r]), 16 * np.finfo(float).eps * c * np.abs(y).max()))
-            bar_s.append(max(1e-6 * abs(ref["s2"][r]), 16 * np.finfo(float).eps * c * psi / n))
+        r = np.flatnonzero(same)
+        bm, bs = parity_bars(w.X, w.Y, ref["sel"][r], np.full(len(r), n), np.full(len(r), d), g,
+                             ref["mean"][r], ref["s2"][r])
         vs_oracle = {"sample": S, "knn_identical_frac": float((idx_g == ref["idx"]).all(axis=1).mean()),
                      "identical_designs_frac": float(same.mean()),
-                     "max_rel_err_mean": max_rel(mg, ref["mean"][same]),
-                     "max_rel_err_s2": max_rel(s2g, ref["s2"][same]),
-                     "max_err_over_parity_bar_mean":
-                         float(np.max(np.abs(mg - ref["mean"][same]) / np.array(bar_m))) if bar_m else None,
-                     "max_err_over_parity_bar_s2":
-                         float(np.max(np.abs(s2g - ref["s2"][same]) / np.array(bar_s))) if bar_s else None}
+                     "max_rel_err_mean": float(np.max(np.abs(mg - ref["mean"][same]) / np.abs(ref["mean"][same]))),
+                     "max_rel_err_s2": float(np.max(np.abs(s2g - ref["s2"][same]) / np.abs(ref["s2"][same]))),
+                     "max_err_over_parity_bar_mean": float(np.max(np.abs(mg - ref["mean"][same]) / bm)),
+                     "max_err_over_parity_bar_s2": float(np.max(np.abs(s2g - ref["s2"][same]) / bs))}
+    # the contract's keys first; then the long measurement sweep and the other
+    # configurations; the decisive extras last (the end of the line is what a
+    # truncated record keeps)
     line = {
         "metric": METRIC, "value": value, "unit": "predictions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -654,17 +704,18 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "N": w.N, "M_per_gpu": M, "p": w.p, "n0": n0, "n": n,
                    "Nprime": Np, "d": d, "g": g, "prec": args.prec, "alc_ctas_per_sm": tuned,
                    "l2": "flushed between timed steps (512 MiB write)"},
-        "cand_evals_per_sec": M * world * E / alc_avg,
-        "alc_kernel_ms": 1e3 * alc_avg,
-        "rmse_vs_truth": rmse, "status_ok_frac": float((st == 0).mean()),
-        "f64_plain": f64,
-        "f64_schur": f64s,
-        "cuda_graph": graph_ms,
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": roofline, "cpu_baseline": cpu, "vs_oracle": vs_oracle, "clocks": clocks,
-        "configs": configs,
+        "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
         "alc_eval_one_location": e1,
+        "configs": configs,
+        "cuda_graph": graph_ms,
+        "f64_plain": f64,
+        "f64_schur": f64s,
+        "rmse_vs_truth": rmse, "status_ok_frac": float((st == 0).mean()),
+        "cand_evals_per_sec": M * world * E / alc_avg,
+        "alc_kernel_ms": 1e3 * alc_avg,
+        "vs_oracle": vs_oracle,
     }
     print(json.dumps(line), flush=True)
 

@@ -60,9 +60,16 @@ typedef enum { LAGP_F64 = 0, LAGP_F32 = 1 } lagp_dtype;
  *                    with Eq. (dxy) in FP64, O(j^2) per candidate per step.
  *  LAGP_PREC_F32BULK candidates screened in FP32 through the Schur-complement
  *                    form of the same criterion (O(j) per candidate per
- *                    step); the leading contenders are re-scored with
- *                    Eq. (dxy) in FP64, and the partitioned-inverse update of
- *                    K_j^{-1} stays in FP64.
+ *                    step); every contender (FP32 score within the
+ *                    contender margin of the FP32 maximum) is re-scored with
+ *                    Eq. (dxy) in double-float arithmetic (FP32 hi/lo pairs,
+ *                    ~48 significant bits) in the Cholesky basis of K_j,
+ *                    whose inverse factor grows by the partitioned inverse
+ *                    of the bordered factor; the argmax is taken on those
+ *                    values.  No FP64 instruction is used (this GPU runs
+ *                    FP64 at 1/64 of the FP32 rate); the double-float
+ *                    Cholesky basis keeps the decisions' and predictions'
+ *                    errors at ~sqrt(cond(K_j)) 2^-48.
  *  LAGP_PREC_F64SCHUR the same Schur-complement form with the candidate
  *                    state in FP64 (the incremental O(j) form of the
  *                    criterion, exact to FP64 rounding); the contenders
@@ -77,15 +84,17 @@ typedef struct lagp_ctx lagp_ctx;
 typedef struct {
     int32_t ctas_per_sm;    /* resident CTAs per SM of the ALC kernels */
     int32_t block_threads;  /* threads per CTA of the ALC kernels */
-    int32_t rescore_max;    /* F32BULK: most candidates re-scored in FP64 per
-                               step, 1..32 (default 8) */
+    int32_t rescore_max;    /* F32BULK: contenders re-scored together in one
+                               batch, 1..32, used up to 8 (default 8); more
+                               contenders take further batches, none is
+                               dropped */
     double rescore_rel;     /* F32BULK: cap of the contender margin (default
-                               0.5).  A candidate is re-scored in FP64 when its
-                               FP32 score is within the margin of the FP32
-                               maximum; the margin is 8x the largest relative
-                               FP32-vs-FP64 score error observed on earlier
-                               re-scores (decaying 0.75x per step), at least
-                               0.02 and at most rescore_rel */
+                               0.5).  A candidate is a contender when its FP32
+                               score is within the margin of the FP32 maximum;
+                               the margin is 8x the largest relative
+                               FP32-vs-double-float score error observed on
+                               earlier re-scores (decaying 0.75x per step), at
+                               least 0.02 and at most rescore_rel */
     int32_t knn_path;       /* kNN collection pass (lagp_knn): 0 = automatic
                                (tcgen05 tensor cores, FP16 split products,
                                for p <= 20; CUDA cores otherwise), 1 = CUDA
@@ -119,9 +128,9 @@ lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in);
 int64_t lagp_launch_count(const lagp_ctx *ctx);
 
 /* Work counters of the FP32-bulk ALC search (not part of the paper's method;
- * they measure the FP64 re-score that the FP32 screen leaves, Eq. dxy):
+ * they measure the double-float re-score that the FP32 screen leaves, Eq. dxy):
  *   out[0]  locations searched
- *   out[1]  sum over steps of the contenders re-scored in FP64 (n_c)
+ *   out[1]  sum over steps of the contenders re-scored (n_c)
  *   out[2]  sum over steps of n_c * j   (j = design size at the step)
  *   out[3]  sum over steps of n_c * j^2
  * summed over every F32BULK search launched on this context since it was
@@ -130,11 +139,19 @@ int64_t lagp_launch_count(const lagp_ctx *ctx);
 lagp_status lagp_alc_work(lagp_ctx *ctx, uint64_t out[4]);
 
 /* Diagnostic: the library's own FP64 exponential (Tang's table-driven
- * method, used for the kernel values of the FP32-bulk re-score) and the CUDA
+ * method, used for the kernel values of the FP64 kernels) and the CUDA
  * library's exp, both evaluated at the n device values a[] into the device
  * arrays out_tang[] and out_lib[] (enqueued on the context's stream). */
 lagp_status lagp_exp64_check(lagp_ctx *ctx, const double *a, int64_t n, double *out_tang,
                              double *out_lib);
+
+/* Diagnostic of the double-float arithmetic of the FP32-bulk search: for
+ * each of the n device doubles a[i], split[2i] and split[2i+1] (device
+ * floats) receive its double-float split hi + lo (hi rounded to nearest, the
+ * split done on the integer pipe), and ex[2i], ex[2i+1] the double-float
+ * exponential of hi + lo (Tang's method in double-float arithmetic).
+ * Enqueued on the context's stream. */
+lagp_status lagp_df_check(lagp_ctx *ctx, const double *a, int64_t n, float *split, float *ex);
 
 /* Autotuner.  Times the ALC search (a2..a6, or a2..a7 when Y is not NULL) on
  * a sample of the given problem (its first min(M, 16 x SMs) locations) for

@@ -116,7 +116,7 @@ __device__ __forceinline__ void df_fma_acc(dfl &acc, dfl x, dfl y) {
 
 // 1 / y and x / y (y normalised, nonzero): a first quotient from the FP32
 // reciprocal, then one correction with the exact remainder
-__device__ __noinline__ dfl df_div(dfl x, dfl y) {
+static __device__ __noinline__ dfl df_div(dfl x, dfl y) {
     const float r = __frcp_rn(y.hi);
     const float q1 = __fmul_rn(x.hi, r);
     // remainder x - q1 y, computed as a double-word (q1 y exact by TwoProd)
@@ -197,7 +197,7 @@ constexpr float DF_EXP_L_HI = 0x1.62e430p-11f;   // ln 2 / 1024 = L_HI + L_LO
 constexpr float DF_EXP_L_LO = -0x1.05c610p-39f;  //   to 1.3e-16 relative
 constexpr float DF_EXP_SHIFT = 0x1.8p23f;        // rounds to an integer when added
 
-__device__ __noinline__ dfl df_exp(dfl a, const float2 *tab) {
+static __device__ __noinline__ dfl df_exp(dfl a, const float2 *tab) {
     if (!(a.hi >= -87.0f)) return df_zero();  // also NaN -> 0 (never produced by the kernels)
     const float t = __fmaf_rn(a.hi, DF_EXP_INV_L, DF_EXP_SHIFT);
     const int N = __float_as_int(t) - __float_as_int(DF_EXP_SHIFT);

@@ -76,6 +76,7 @@ def _load():
     lib.lagp_alc_eval.argtypes = [P, P, I64, I32, ctypes.c_int, P, P, I32, P, I64, D, D, P, P]
     lib.lagp_scale_inputs.argtypes = [P, P, I64, I32, ctypes.c_int, P, P]
     lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
+    lib.lagp_df_check.argtypes = [P, P, I64, P, P]
     lib.lagp_knn_tc_dist.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P]
     lib.lagp_knn_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I32)]
     lib.lagp_knn_tc_stall.argtypes = [P]
@@ -83,7 +84,7 @@ def _load():
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
-              "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_alc_eval",
+              "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_df_check", "lagp_alc_eval",
               "lagp_scale_inputs", "lagp_knn_tc_dist", "lagp_knn_stats", "lagp_knn_tc_stall"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
@@ -238,6 +239,18 @@ def exp64_check(a: torch.Tensor):
     _check(_lib.lagp_exp64_check(ctx, pa, a.numel(), ctypes.c_void_p(t.data_ptr()),
                                  ctypes.c_void_p(l.data_ptr())), ctx, "lagp_exp64_check")
     return t, l
+
+
+def df_check(a: torch.Tensor):
+    """The double-float split of the FP64 device tensor a and the
+    double-float exp of it.  Returns (split, ex), each [n, 2] float32 (hi, lo)."""
+    pa = _dev(a, "a", torch.float64)
+    ctx = context(a.device)
+    sp = torch.empty((a.numel(), 2), dtype=torch.float32, device=a.device)
+    ex = torch.empty_like(sp)
+    _check(_lib.lagp_df_check(ctx, pa, a.numel(), ctypes.c_void_p(sp.data_ptr()),
+                              ctypes.c_void_p(ex.data_ptr())), ctx, "lagp_df_check")
+    return sp, ex
 
 
 def lagp_knn(X: torch.Tensor, Xref: torch.Tensor, Nprime_max: int, Nprime=None):

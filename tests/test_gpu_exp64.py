@@ -53,3 +53,47 @@ def test_exp64_against_cuda_and_exact(L):
         err = abs(Decimal(float(tang[i])) - exact) / Decimal(ulp(e))
         worst = max(worst, float(err))
     assert worst <= 1.0, worst
+
+
+def test_double_float_split_and_exp(L):
+    """The FP32-bulk search's double-float arithmetic: the split of a double
+    into hi + lo on the integer pipe (hi the round-to-nearest FP32 value, the
+    pair within 2^-47 of the double), and Tang's exponential in double-float
+    against the exact exponential of hi + lo (60-digit decimal) for the
+    kernel values' range a in [-87, 0]."""
+    rng = np.random.default_rng(12)
+    mags = np.concatenate([rng.uniform(-1, 1, 20_000), rng.uniform(-3, 3, 5_000) * 10.0 ** rng.integers(-20, 20, 5_000),
+                           np.array([0.0, -0.0, 1.0, -1.0, 0.5, 1e-30, -1e-30, 3e38, -3e38])])
+    sp, _ = (t.cpu().numpy() for t in L.df_check(torch.from_numpy(mags).cuda()))
+    hi, lo = sp[:, 0].astype(np.float64), sp[:, 1].astype(np.float64)
+    big = np.abs(mags) >= 2.0 ** -74
+    assert np.all(np.abs(hi + lo - mags)[big] <= 2.0 ** -47 * np.abs(mags[big]))
+    # hi is the FP32 value of the double rounded to nearest (ties away from
+    # zero, where numpy rounds ties to even: exact ties need 29 trailing zero bits)
+    f32 = mags.astype(np.float32).astype(np.float64)
+    assert np.mean(hi[big] == f32[big]) > 0.999
+    assert np.all(np.abs(hi - f32)[big] <= np.spacing(np.abs(f32[big]).astype(np.float32)).astype(np.float64))
+    assert sp[np.flatnonzero(mags == 0.0)].tolist() == [[0.0, 0.0], [0.0, 0.0]]
+    # exponential
+    a = np.concatenate([-rng.uniform(0, 1, 20_000), -rng.exponential(5.0, 20_000), -rng.uniform(0, 87, 20_000),
+                        np.array([0.0, -1e-30, -86.99, -87.5, -100.0, -1000.0])])
+    sp, ex = (t.cpu().numpy() for t in L.df_check(torch.from_numpy(a).cuda()))
+    val = ex[:, 0].astype(np.float64) + ex[:, 1].astype(np.float64)
+    assert np.all(val[a < -87.0] == 0.0)
+    getcontext().prec = 60
+    idx = np.concatenate([rng.choice(np.flatnonzero(a >= -87.0), 4000, replace=False), np.arange(len(a) - 6, len(a) - 3)])
+    worst, worst_abs = 0.0, 0.0
+    for i in idx:
+        x = Decimal(float(sp[i, 0])) + Decimal(float(sp[i, 1]))  # the argument the pair holds
+        exact = x.exp()
+        got = Decimal(float(ex[i, 0])) + Decimal(float(ex[i, 1]))
+        if a[i] >= -70.0:
+            worst = max(worst, float(abs(got - exact) / exact))
+        else:
+            # below e^-70 ~ 2^-101 the low word leaves FP32's normal range and
+            # the pair keeps FP32 precision (such kernel values are negligible
+            # beside the O(1) terms of every sum they enter)
+            worst_abs = max(worst_abs, float(abs(got - exact)))
+    # a few units of 2^-48 (the reduction's and the table's roundings)
+    assert worst <= 2.0 ** -45, worst
+    assert worst_abs <= 2.0 ** -120, worst_abs
