@@ -73,6 +73,22 @@ def workload_for_rank(rank: int, M=None):
     return w
 
 
+def max_over_ranks(t_local, world, device=None):
+    """The slowest rank's time: every rank's timed seconds, MAX-reduced."""
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(M, world, steps, t_max):
+    """Whole-job predictions per second: every rank predicts its own M
+    locations each step (weak scaling), the slowest rank sets the time."""
+    return M * world * steps / t_max
+
+
 def work_per_location(n0, n, Np):
     """ALC candidate evaluations of one location's greedy search,
     E = sum_{j=n0}^{n-1} (N' - j)."""
@@ -515,11 +531,8 @@ def run_ours(args, rank, world, local_rank):
     work = L.alc_work(dev)
     clocks = clk.stop() if clk else None
     t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = M * world * args.steps / t_max
+    t_max = max_over_ranks(t_local, world, dev)
+    value = aggregate_rate(M, world, args.steps, t_max)
 
     # parity spot-check of this run's output: statuses and RMSE to the truth
     st = s["status"].cpu().numpy()
@@ -625,10 +638,8 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             L.lagp_agp(Xh, Yh, Xrh, n0, n, Np, d, g, prec=args.prec, device=local_rank)
             e2e_s.append(time.perf_counter() - t0)
-        te = torch.tensor([statistics.mean(e2e_s)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": M * world / float(te.item()), "unit": "predictions/s",
+        te = max_over_ranks(statistics.mean(e2e_s), world, dev)
+        e2e = {"value": aggregate_rate(M, world, 1, te), "unit": "predictions/s",
                "h2d_bytes_per_step": Xh.nbytes + Yh.nbytes + Xrh.nbytes + 2 * M * 4,
                "d2h_bytes_per_step": 4 * M * 8 + 4 * M * 4}
 

@@ -30,7 +30,8 @@
  *    returns LAGP_OK, status[m] receives LAGP_ENOTPD (a local covariance
  *    matrix that is not positive definite in floating point) and that
  *    location's floating outputs are NaN (its index outputs -1).
- *  - M = 0 is a no-op that returns LAGP_OK.
+ *  - M = 0 is a no-op that returns LAGP_OK; M must be below 2^30 (the
+ *    persistent kernels count locations with a 32-bit atomic counter).
  *  - A context must not be used from two host threads at once.
  */
 #ifndef LAGP_H

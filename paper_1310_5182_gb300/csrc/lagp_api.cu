@@ -162,6 +162,10 @@ __global__ void fill_f64_kernel(double *p, int64_t n, double v) {
         p[i] = v;
 }
 
+// The persistent kernels hand out locations through a 32-bit atomic counter
+// that runs up to M plus the grid size: M stays below 2^30.
+constexpr int64_t LAGP_M_LIMIT = (int64_t)1 << 30;
+
 static lagp_status check_design(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
                                 lagp_dtype dtype, const char *fn) {
     if (!X) return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": X is NULL");
@@ -179,7 +183,7 @@ lagp_status lagp_knn(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dt
     if (!ctx) return LAGP_EINVAL;
     ctx->err.clear();
     LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_knn"));
-    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: M < 0");
+    if (M < 0 || M >= LAGP_M_LIMIT) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: need 0 <= M < 2^30");
     if (M == 0) return LAGP_OK;
     if (!Xref || !idx) return lagp_fail(ctx, LAGP_EINVAL, "lagp_knn: NULL Xref or idx");
     if (Nprime_max < 1 || Nprime_max > N)
@@ -224,7 +228,7 @@ static lagp_status alc_common(lagp_ctx *ctx, const char *fn, const void *X, int6
     ctx->err.clear();
     const std::string f(fn);
     LAGP_TRY(check_design(ctx, X, N, p, dtype, fn));
-    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, f + ": M < 0");
+    if (M < 0 || M >= LAGP_M_LIMIT) return lagp_fail(ctx, LAGP_EINVAL, f + ": need 0 <= M < 2^30");
     if (M == 0) return LAGP_OK;
     if (!Xref || !idx || !d || !sel || !status)
         return lagp_fail(ctx, LAGP_EINVAL, f + ": NULL required array");
@@ -269,7 +273,7 @@ lagp_status lagp_alc_predict(lagp_ctx *ctx, const void *X, const void *Y, int64_
 
 static lagp_status check_gp(lagp_ctx *ctx, const GpArgs &a, const char *fn, bool need_ref) {
     LAGP_TRY(check_design(ctx, a.X, a.N, a.p, a.dtype, fn));
-    if (a.M < 0) return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": M < 0");
+    if (a.M < 0 || a.M >= LAGP_M_LIMIT) return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": need 0 <= M < 2^30");
     if (a.M == 0) return LAGP_OK;
     if (!a.Y || !a.sel || (need_ref && !a.Xref))
         return lagp_fail(ctx, LAGP_EINVAL, std::string(fn) + ": NULL required array");
@@ -340,7 +344,7 @@ lagp_status lagp_agp(lagp_ctx *ctx, const void *X, const void *Y, int64_t N, int
     if (!ctx) return LAGP_EINVAL;
     ctx->err.clear();
     LAGP_TRY(check_design(ctx, X, N, p, dtype, "lagp_agp"));
-    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: M < 0");
+    if (M < 0 || M >= LAGP_M_LIMIT) return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: need 0 <= M < 2^30");
     if (M == 0) return LAGP_OK;
     if (!Y || !Xref || !mean || !s2 || !df || !status)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_agp: NULL required array");

@@ -209,11 +209,14 @@ extern "C" lagp_status lagp_predict_noalloc(lagp_ctx *ctx, const void *X, const 
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_noalloc: NULL required array");
     if (N < 1 || N >= (int64_t)INT32_MAX || p < 1 || p > 64 || (dtype != LAGP_F64 && dtype != LAGP_F32))
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_noalloc: need 1 <= N < 2^31, 1 <= p <= 64, dtype F64/F32");
-    if (M < 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_noalloc: M < 0");
+    // (its work counter is a 32-bit atomic that runs up to M + NA_CTAS)
+    if (M < 0 || M >= ((int64_t)1 << 30))
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_noalloc: need 0 <= M < 2^30");
     if (n_max < 1 || n_max > NA_NMAX)
         return lagp_fail(ctx, LAGP_EINVAL,
                          "lagp_predict_noalloc: n_max must be in [1, 64], the size of the static scratch");
-    if (!(g >= 0.0)) return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_noalloc: g must be >= 0");
+    if (!(g >= 0.0) || !isfinite(g))
+        return lagp_fail(ctx, LAGP_EINVAL, "lagp_predict_noalloc: g must be finite and >= 0");
     if (M == 0) return LAGP_OK;
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
     double *scratch = nullptr;

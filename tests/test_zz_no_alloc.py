@@ -5,7 +5,12 @@ cannot take cudaMalloc's implicit synchronisation).  Its scratch is a fixed
 array inside the library shared by every call, so this file checks it on two
 calls in a row, each against the ordinary lagp_predict on the same inputs,
 with the tolerance the parity tests use (relative 1e-6, or 16 eps cond(K_n)
-times the quantity's scale).  The file is collected last on purpose."""
+times the quantity's scale).  It also checks the per-location failure
+statuses against lagp_predict's (the paths where a stale matrix from the
+previous call could leak into the output) and the values directly against
+the FP64 oracle.  The file is collected last on purpose."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -80,6 +85,47 @@ def test_predict_noalloc_matches_predict_twice():
     assert (ref["status"] == 0).all()
 
 
+def test_predict_noalloc_failure_statuses_and_oracle():
+    """Failed locations between valid ones, right after a call that filled
+    the scratch: a design row out of range, n = 0, d <= 0 (LAGP_EINVAL) and
+    a repeated design row with no nugget (LAGP_ENOTPD) must get the same
+    status and NaN outputs as lagp_predict; the valid locations must match
+    the FP64 oracle's predictions within the parity bar."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1310_5182_gb300 as L
+    from oracle import oracle as O
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+
+    w = W.borehole(seed=35, N=20_000, M=8, Np=200, n=8)
+    X, Y, Xr, sel = _case(L, w, 8, w.d)
+    sel_np = sel.cpu().numpy().copy()
+    n_arr = np.full(8, 8, np.int32)
+    d = np.full(8, w.d)
+    g = 0.0
+    sel_np[0, 3] = w.N + 5          # row out of range
+    n_arr[1] = 0                    # empty design
+    d[2] = -1.0                     # non-positive lengthscale
+    sel_np[3, 1] = sel_np[3, 0]     # repeated row, no nugget: K_n singular
+    sel_bad = torch.from_numpy(sel_np).cuda()
+    got = L.lagp_predict_noalloc(X, Y, Xr, sel_bad, n_arr, d, g)
+    ref = L.lagp_predict(X, Y, Xr, sel_bad, n_arr, d, g)
+    torch.cuda.synchronize()
+    st_g, st_r = got["status"].cpu().numpy(), ref["status"].cpu().numpy()
+    assert np.array_equal(st_g, st_r), (st_g, st_r)
+    assert list(st_g[:4]) == [1, 1, 1, 2] and (st_g[4:] == 0).all()
+    for k in ("mean", "s2", "df"):
+        a_, b_ = got[k].cpu().numpy(), ref[k].cpu().numpy()
+        assert np.isnan(a_[:4]).all() and np.isnan(b_[:4]).all()
+    ok = np.arange(4, 8)
+    orc = O.predict(w.X, w.Y, w.Xref[ok], sel_np[ok], n_arr[ok], d[ok], g)
+    am, a2 = _tolerances(w.X, w.Y, sel_np[ok], n_arr[ok], d[ok], g)
+    mg, sg = got["mean"].cpu().numpy()[ok], got["s2"].cpu().numpy()[ok]
+    assert np.all(np.abs(mg - orc["mean"]) <= np.maximum(1e-6 * np.abs(orc["mean"]), am))
+    assert np.all(np.abs(sg - orc["s2"]) <= np.maximum(1e-6 * np.abs(orc["s2"]), a2))
+
+
 def test_predict_noalloc_rejects_sizes_beyond_its_scratch():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -89,3 +135,6 @@ def test_predict_noalloc_rejects_sizes_beyond_its_scratch():
     X, Y, Xr, sel = _case(L, w, 65, w.d)
     with pytest.raises(L.LagpError, match="n_max must be in"):
         L.lagp_predict_noalloc(X, Y, Xr, sel, 65, w.d, w.g)
+    # an infinite nugget is rejected like lagp_predict rejects it
+    with pytest.raises(L.LagpError, match="g must be finite"):
+        L.lagp_predict_noalloc(X, Y, Xr, sel[:, :64].contiguous(), 64, w.d, float("inf"))
