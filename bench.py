@@ -290,6 +290,28 @@ def vs_oracle_leg(w, out, S, seed=7):
     res = {"sample": S, "oracle_s": round(sec, 2),
            "knn_identical_frac": float((out["idx"][samp][:, :ref["idx"].shape[1]] == ref["idx"]).all(axis=1).mean()),
            "identical_designs_frac": float(same.mean())}
+    # each design that differs, at its first differing step: a near tie (the
+    # oracle's own criterion values put the GPU's pick within a relative 1e-6,
+    # or 16 eps / g, of the best) or a miss (its relative gap reported)
+    div = np.flatnonzero(~same)
+    if div.size:
+        top = O.alc_select(w.X, w.Xref[samp[div]], ref["idx"][div], w.n0, w.n[samp[div]], w.d, w.g,
+                           Np=w.Np[samp[div]], nmax=nmax, topk=4)
+        near, gaps = 0, []
+        for q, r in enumerate(div):
+            j = int(np.flatnonzero(sel_g[r, :w.n[samp[r]]] != ref["sel"][r, :w.n[samp[r]]])[0])
+            ti, tv = list(top["top_idx"][q, j]), top["top_val"][q, j]
+            pick = int(sel_g[r, j])
+            gap = (tv[0] - tv[ti.index(pick)]) if pick in ti else np.inf
+            if gap <= max(1e-6 * abs(tv[0]), 16 * np.finfo(float).eps / w.g):
+                near += 1
+            else:
+                gaps.append(float(gap / abs(tv[0])) if np.isfinite(gap) else None)
+        res["near_tie_divergences"] = near
+        res["misses"] = len(gaps)
+        res["miss_rel_gaps"] = gaps[:20]
+    else:
+        res["near_tie_divergences"] = res["misses"] = 0
     if w.mle is not None:
         d_g = out["d"][samp]
         res["max_rel_err_d"] = float(np.max(np.abs(d_g[same] - d_ref[same]) / d_ref[same])) if same.any() else None
@@ -315,31 +337,44 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
     Npm, nmax = int(w.Np.max()), int(w.n.max())
     stream = torch.cuda.current_stream(dev)
 
-    def step():
+    def step(ev=None):
+        # ev: events between the stages (kNN | search | MLE | prediction)
+        mark = (lambda i: ev[i].record(stream)) if ev else (lambda i: None)
         idx, st = L.lagp_knn(X, Xr, Npm, Nprime=Np_t)
+        mark(0)
         if w.mle is None:
             out = L.lagp_alc_predict(X, Y, Xr, idx, w.n0, n_t, w.d, w.g, prec=prec, Nprime=Np_t,
                                      n_max=nmax)
+            mark(1)
             return dict(idx=idx, sel=out["sel"], mean=out["mean"], s2=out["s2"]), [st, out["status"]]
         s = L.lagp_alc_select(X, Xr, idx, w.n0, n_t, w.d, w.g, prec=prec, Nprime=Np_t, n_max=nmax)
+        mark(1)
         m = L.lagp_mle_step(X, Y, s["sel"], n_t, w.d, w.g, *w.mle)
+        mark(2)
         pr = L.lagp_predict(X, Y, Xr, s["sel"], n_t, m["d"], w.g)
         return (dict(idx=idx, sel=s["sel"], d=m["d"], mean=pr["mean"], s2=pr["s2"]),
                 [st, s["status"], m["status"], pr["status"]])
 
     for _ in range(warmup):
         step()
-    times = []
+    times, stages = [], []
+    L.mle_work(dev)  # reset: the timed steps' counts follow
     for _ in range(steps):
         if flush is not None:
             flush.zero_()
         torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        outs, sts = step()
-        e1.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        ev[0].record(stream)
+        outs, sts = step(ev[1:4])
+        ev[4].record(stream)
         torch.cuda.synchronize(dev)
-        times.append(e0.elapsed_time(e1))
+        times.append(ev[0].elapsed_time(ev[4]))
+        if w.mle is None:
+            stages.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), 0.0, ev[2].elapsed_time(ev[4])])
+        else:
+            stages.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
+                           ev[3].elapsed_time(ev[4])])
+    mw = L.mle_work(dev)
     ok = np.all([t.cpu().numpy() == 0 for t in sts], axis=0)
     outs = {k: v.cpu().numpy() for k, v in outs.items()}
     mean = outs["mean"]
@@ -349,6 +384,22 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
            "Nprime": [int(w.Np.min()), int(w.Np.max())], "dtype": str(w.X.dtype), "prec": prec,
            "mle": list(w.mle) if w.mle else None, "status_ok_frac": float(ok.mean()),
            "rmse_vs_truth": float(np.sqrt(np.mean((mean[ok] - w.truth[ok]) ** 2)))}
+    st_ms = np.mean(np.array(stages), axis=0)
+    if w.mle is None:
+        res["stage_ms"] = {"knn": round(st_ms[0], 3), "search_predict": round(st_ms[1], 3)}
+    else:
+        res["stage_ms"] = {"knn": round(st_ms[0], 3), "search": round(st_ms[1], 3), "mle": round(st_ms[2], 3),
+                           "predict": round(st_ms[3], 3)}
+        # the Newton MLE's FP64 work, counted by the kernel (n^3/3 flops a
+        # factorisation, 2 n^3 a derivative evaluation), against the FP64 peak
+        # from the unit counts (2 FMA lanes a cycle an SM) at the maximum clock
+        fl = (mw["llik_n3"] / 3 + 2 * mw["derivs_n3"]) / steps
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 4 * 2070e6 / 1e12
+        ach = fl / (st_ms[2] / 1e3) / 1e12
+        res["mle_roofline"] = {"bound": "alu", "kernel": "mle_kernel", "unit": "TFLOP/s", "achieved": ach,
+                               "peak": peak, "frac": ach / peak, "fp64_flops_per_launch": fl,
+                               "peak_source": f"derived: FP64 FMA, {sms} SMs x 4 flop/cycle x 2070 MHz"}
     if oracle_S:
         res["vs_oracle"] = vs_oracle_leg(w, outs, oracle_S)[0]
     return res

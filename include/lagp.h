@@ -139,6 +139,17 @@ int64_t lagp_launch_count(const lagp_ctx *ctx);
  * resets the counters to zero. */
 lagp_status lagp_alc_work(lagp_ctx *ctx, uint64_t out[4]);
 
+/* Work counters of the Newton MLE of d (lagp_mle_step; not part of the
+ * paper's method, they give its FP64 operation count, Eq. gpk):
+ *   out[0]  sum over likelihood evaluations of n^3 (each factorises K_n:
+ *           ~n^3/3 flops)
+ *   out[1]  sum over derivative evaluations of n^3 (L^{-1}, K^{-1} and
+ *           L^{-1} K' L^{-T}: ~2 n^3 flops)
+ * summed over every lagp_mle_step launched on this context since it was
+ * created or last read.  Reading synchronises the context's stream and
+ * resets the counters to zero. */
+lagp_status lagp_mle_work(lagp_ctx *ctx, uint64_t out[2]);
+
 /* Diagnostic: the library's own FP64 exponential (Tang's table-driven
  * method, used for the kernel values of the FP64 kernels) and the CUDA
  * library's exp, both evaluated at the n device values a[] into the device

@@ -10,7 +10,7 @@ library has not been built: there is no CPU fallback.  The build module
 _BINDING = ("LagpError", "context", "get_tuning", "lagp_agp", "lagp_alc_predict", "lagp_alc_select",
             "lagp_knn", "lagp_autotune", "lagp_alc_eval", "lagp_scale_inputs",
             "lagp_mle_step", "lagp_predict", "lagp_predict_grad", "lagp_predict_noalloc",
-            "launch_count", "library", "alc_work", "exp64_check", "df_check", "lagp_knn_tc_dist", "knn_stats", "knn_tc_stall",
+            "launch_count", "library", "alc_work", "mle_work", "exp64_check", "df_check", "lagp_knn_tc_dist", "knn_stats", "knn_tc_stall",
             "set_tuning")
 
 __all__ = list(_BINDING)

@@ -118,8 +118,10 @@ __host__ __device__ __forceinline__ int b32_ldl(int nmax) { return nmax | 1; }  
 __host__ __device__ __forceinline__ int b32_ldc(int nmax) { return (nmax + 2) & ~1; }  // >= nmax + 1
 __host__ __device__ __forceinline__ int b32_ldx(int nmax) { return (nmax + 1) & ~1; }  // >= nmax
 
-// the double-float group's barrier (named barrier 1, its 128 threads)
+// the double-float group's barrier (named barrier 1, its 128 threads) and the
+// FP32 group's (named barrier 2)
 __device__ __forceinline__ void dsync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void fsync() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
 __device__ __forceinline__ float f32_score(float cov, float v, float gf) {
     return __fdividef(cov * cov, fmaxf(v, gf));
@@ -234,12 +236,15 @@ alc_bulk32_kernel(B32Params P) {
     float2 *con_u = con_k + tmax * ldc;                    // tmax x ldc: u_c = L^{-1} k_j(x_c)
     float2 *cpart = con_u + tmax * ldc;                    // WARPS x ldc partial contractions
     float2 *con_x = cpart + WARPS * ldc;                   // tmax x p: the batch's coordinates
+    float2 *win_u = con_x + tmax * p;                      // ldc: the running best's u (several batches)
+    float2 *win_x = win_u + ldc;                           // p (even): its coordinates
     // NPAD: FP32 v of every candidate (16-byte aligned for vector loads)
-    float *v_s = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(con_x + tmax * p) + 15) & ~(uintptr_t)15);
+    float *v_s = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(win_x + ((p + 1) & ~1)) + 15) & ~(uintptr_t)15);
     float *r_s = v_s + NPAD;                               // NPAD: FP32 r of every candidate
 
-    __shared__ int s_loc, s_bad, s_total, s_ncon, s_nb, s_next, s_wl;
+    __shared__ int s_loc, s_bad, s_total, s_wl, s_save, s_win_saved;
     __shared__ float w_max[FWARPS];
+    __shared__ int w_cnt[FWARPS];
     // contender list (the first LCAP; the rest in the per-CTA global list),
     // each with the FP32 pivot data of its candidate
     __shared__ int lst_slot[LCAP];
@@ -248,6 +253,7 @@ alc_bulk32_kernel(B32Params P) {
     __shared__ int bat_slot[TMAX_CAP], bat_row[TMAX_CAP];
     __shared__ float bat_s[TMAX_CAP], bat_v[TMAX_CAP], bat_r[TMAX_CAP];
     __shared__ float2 con_y[TMAX_CAP], con_v[TMAX_CAP], con_r[TMAX_CAP], con_ry[TMAX_CAP];
+    __shared__ float2 win_s[3];  // the running best's v, r, y - z^T u (several batches)
     __shared__ int best_slot, best_row;
     __shared__ float best_v, best_r;
     __shared__ float2 best_dl;
@@ -403,12 +409,17 @@ alc_bulk32_kernel(B32Params P) {
                     const int t = __shfl_up_sync(LAGP_FULL_MASK, incl, o);
                     if (lane >= o) incl += t;
                 }
-                const int wtot = __shfl_sync(LAGP_FULL_MASK, incl, 31);
-                int base = 0;
-                if (lane == 31 && wtot > 0) base = atomicAdd(&s_total, wtot);
-                base = __shfl_sync(LAGP_FULL_MASK, base, 31);
-                // list order depends on the warps' arrival; the contender set,
-                // and every result, does not
+                // the list in slot order (the batches below are its chunks, so
+                // that every result is independent of the warps' timing)
+                if (lane == 31) w_cnt[warp] = incl;
+                fsync();
+                int base = 0, all = 0;
+#pragma unroll
+                for (int w = 0; w < FWARPS; w++) {
+                    base += w < warp ? w_cnt[w] : 0;
+                    all += w_cnt[w];
+                }
+                if (tid == 0) s_total = all;
                 int pos = base + incl - mine;
                 for (unsigned f = flags; f; f &= f - 1, pos++) {
                     const int c = c0 + __ffs(f) - 1;
@@ -426,9 +437,9 @@ alc_bulk32_kernel(B32Params P) {
                     }
                 }
             } else if (dt == 0) {
-                s_nb = 0;
                 s_steperr = 0.f;
                 best_slot = -1;
+                s_win_saved = 0;
                 best_row = INT32_MAX;
                 best_dl = make_float2(-FLT_MAX, 0.f);
             }
@@ -536,85 +547,29 @@ alc_bulk32_kernel(B32Params P) {
                 for (int q = 1; q < DWARPS; q++) b = df_add_sloppy(b, ld2(cpart + q * ldc + dt));
                 st2(LT + dt * ldl + j - 1, df_neg(df_mul(df_normalize(b), ld2(&s_il))));
             }
-            // Re-score in batches of at most tmax contenders (one batch holding
-            // every contender when there are at most tmax of them, the rule); a
-            // final batch of one recomputes the winner's vectors when it came
-            // from an earlier batch
-            int remaining = total;
-            bool final_pass = false;
-            for (;;) {
-                // ---- form the batch and stage its coordinates and responses
-                if (!final_pass && total <= tmax) {
-                    // the list is the batch: copied and staged without a barrier
-                    if (dt < total) {
-                        const int slot = lst_slot[dt];
-                        bat_slot[dt] = slot;
-                        bat_row[dt] = cands[slot];
-                        bat_s[dt] = lst_s[dt];
-                        bat_v[dt] = lst_v[dt];
-                        bat_r[dt] = lst_r[dt];
-                        if (fused) con_y[dt] = Yc[slot];
-                    }
-                    for (int e = dt; e < total * p; e += DTHREADS) {
-                        const int w = e / p, i = e - w * p, slot = lst_slot[w];
-                        con_x[e] = make_float2(Cg[i * NPAD + slot], x64 ? Clo[i * NPAD + slot] : 0.f);
-                    }
-                    if (dt == 0) s_ncon = total;
-                } else {
-                    if (!final_pass) {
-                        // the best tmax of the remaining by FP32 score, ties to
-                        // the lower row; taken entries are marked with slot -1
-                        if (dw == 0) {
-                            int nb = 0;
-                            for (; nb < tmax; nb++) {
-                                float bs = -FLT_MAX;
-                                int brow = INT32_MAX, bpos = -1;
-                                for (int e = lane; e < total; e += 32) {
-                                    const int sl = e < LCAP ? lst_slot[e] : ov_slot[e];
-                                    if (sl < 0) continue;
-                                    const float sc = e < LCAP ? lst_s[e] : ov_s[e];
-                                    const int rw = cands[sl];
-                                    if (sc > bs || (sc == bs && rw < brow)) {
-                                        bs = sc;
-                                        brow = rw;
-                                        bpos = e;
-                                    }
-                                }
-                                alc::warp_best3(bs, brow, bpos);
-                                if (bpos < 0) break;
-                                if (lane == 0) {
-                                    const bool lo = bpos < LCAP;
-                                    bat_slot[nb] = lo ? lst_slot[bpos] : ov_slot[bpos];
-                                    bat_row[nb] = brow;
-                                    bat_s[nb] = bs;
-                                    bat_v[nb] = lo ? lst_v[bpos] : ov_v[bpos];
-                                    bat_r[nb] = lo ? lst_r[bpos] : ov_r[bpos];
-                                    if (lo) lst_slot[bpos] = -1;
-                                    else ov_slot[bpos] = -1;
-                                }
-                                __syncwarp();
-                            }
-                            if (lane == 0) s_ncon = nb;
-                        }
-                    } else if (dt == 0) {
-                        bat_slot[0] = best_slot;
-                        bat_row[0] = best_row;
-                        bat_s[0] = 0.f;
-                        bat_v[0] = best_v;
-                        bat_r[0] = best_r;
-                        s_ncon = 1;
-                    }
-                    dsync();
-                    for (int w = dw; w < s_ncon; w += DWARPS) {
-                        const int slot = bat_slot[w];
-                        for (int i = lane; i < p; i += 32)
-                            con_x[w * p + i] = make_float2(Cg[i * NPAD + slot], x64 ? Clo[i * NPAD + slot] : 0.f);
-                        if (fused && lane == 0) con_y[w] = Yc[slot];
-                    }
+            // Re-score in batches of at most tmax contenders, the consecutive
+            // chunks of the list (one batch holding every contender when there
+            // are at most tmax of them, the rule); when the running best
+            // improves in a batch that others follow, its vectors are kept
+            // (win_*) for the winner's phase
+            for (int b0 = 0; b0 < total; b0 += tmax) {
+                const int ncon = min(tmax, total - b0), remaining = total - b0 - ncon;
+                // ---- the batch: its list entries, coordinates and responses
+                if (dt < ncon) {
+                    const int e = b0 + dt, slot = e < LCAP ? lst_slot[e] : ov_slot[e];
+                    bat_slot[dt] = slot;
+                    bat_row[dt] = cands[slot];
+                    bat_s[dt] = e < LCAP ? lst_s[e] : ov_s[e];
+                    bat_v[dt] = e < LCAP ? lst_v[e] : ov_v[e];
+                    bat_r[dt] = e < LCAP ? lst_r[e] : ov_r[e];
+                    if (fused) con_y[dt] = Yc[slot];
+                }
+                for (int e2 = dt; e2 < ncon * p; e2 += DTHREADS) {
+                    const int w = e2 / p, i = e2 - w * p, e = b0 + w;
+                    const int slot = e < LCAP ? lst_slot[e] : ov_slot[e];
+                    con_x[e2] = make_float2(Cg[i * NPAD + slot], x64 ? Clo[i * NPAD + slot] : 0.f);
                 }
                 dsync();
-                const int ncon = s_ncon;
-                if (!final_pass) remaining -= ncon;
                 // ---- R1: k_j(x_c) (t < j) and K(x_c, x) (t = j) in double-float;
                 // each squared distance split over G lanes (G in 1, 2, 4)
                 {
@@ -648,15 +603,33 @@ alc_bulk32_kernel(B32Params P) {
                     }
                 }
                 dsync();
-                // ---- R2: u_c = L^{-1} k_j(x_c), each contender's rows split
-                // over wpc warps
+                // ---- R2: u_c = L^{-1} k_j(x_c): with one or two contenders
+                // each contender's rows split over wpc warps; with more, one
+                // thread per (contender, t) over the whole group (two
+                // accumulation chains), so that the chains are j/2 long
                 const int wpc = ncon == 1 ? 4 : (ncon == 2 ? 2 : 1);
-                if (j > 0)
-                    for (int item = dw; item < ncon * wpc; item += DWARPS) {
-                        const int w = item / wpc, part = item - w * wpc;
-                        df_tri_lower(con_k + w * ldc, LT, ldl, part * j / wpc, (part + 1) * j / wpc, j, lane,
-                                     cpart + item * ldc);
+                if (j > 0) {
+                    if (ncon >= 3) {
+                        for (int e = dt; e < ncon * j; e += DTHREADS) {
+                            const int w = e / j, t = e - w * j;
+                            const float2 *kc = con_k + w * ldc;
+                            dfl a0 = df_zero(), a1 = df_zero();
+                            int s = 0;
+                            for (; s < t; s += 2) {
+                                df_fma_acc(a0, ld2(LT + s * ldl + t), ld2(kc + s));
+                                df_fma_acc(a1, ld2(LT + (s + 1) * ldl + t), ld2(kc + s + 1));
+                            }
+                            if (s == t) df_fma_acc(a0, ld2(LT + s * ldl + t), ld2(kc + s));
+                            st2(cpart + w * ldc + t, df_add(df_normalize(a0), df_normalize(a1)));
+                        }
+                    } else {
+                        for (int item = dw; item < ncon * wpc; item += DWARPS) {
+                            const int w = item / wpc, part = item - w * wpc;
+                            df_tri_lower(con_k + w * ldc, LT, ldl, part * j / wpc, (part + 1) * j / wpc, j, lane,
+                                         cpart + item * ldc);
+                        }
                     }
+                }
                 dsync();
                 // ---- R3: u_c from the partials; |u_c|^2, w^T u_c, z^T u_c by
                 // one warp per contender -> v_c, r_c and (fused) y_c - z^T u_c.
@@ -735,8 +708,7 @@ alc_bulk32_kernel(B32Params P) {
                                 bv = bat_v[lane];
                                 bc = bat_r[lane];
                             }
-                            // (the winner's batch of one repeats a contender: no new sample)
-                            if (j >= a.n0 && !final_pass && dl.hi > 0.f)
+                            if (j >= a.n0 && dl.hi > 0.f)
                                 err = fabsf(__fdividef(bat_s[lane], dl.hi) - 1.f);
                         }
                     }
@@ -764,32 +736,38 @@ alc_bulk32_kernel(B32Params P) {
                     if (lane == 0) {
                         s_steperr = fmaxf(s_steperr, err);
                         const dfl bd = ld2(&best_dl);
-                        if (slot >= 0 && (df_gt(dl, bd) || (!df_gt(bd, dl) && row < best_row))) {
+                        const bool improved = slot >= 0 && (df_gt(dl, bd) || (!df_gt(bd, dl) && row < best_row));
+                        if (improved) {
                             st2(&best_dl, dl);
                             best_row = row;
                             best_slot = slot;
                             best_v = bv;
                             best_r = bc;
+                            s_wl = wl;
+                            s_win_saved = remaining > 0;  // (copied below: later batches overwrite)
                         }
-                        s_wl = wl;
-                        s_nb += 1;
-                        // what follows this batch: 0 another batch, 1 a final
-                        // batch of the winner alone (its vectors are from an
-                        // earlier batch), 2 done
-                        s_next = final_pass ? 2 : remaining > 0 ? 0 : (s_nb == 1 || slot == best_slot) ? 2 : 1;
-                        if (!final_pass) {
-                            s_work[1] += (unsigned long long)ncon;
-                            s_work[2] += (unsigned long long)ncon * j;
-                            s_work[3] += (unsigned long long)ncon * j * j;
-                        }
+                        s_save = improved && remaining > 0;
+                        s_work[1] += (unsigned long long)ncon;
+                        s_work[2] += (unsigned long long)ncon * j;
+                        s_work[3] += (unsigned long long)ncon * j * j;
                     }
                 }
                 dsync();
-                // (s_next is written again only after this batch's successor has
-                // passed four more barriers, so every thread reads this value)
-                const int next = s_next;
-                if (next == 2) break;
-                if (next == 1) final_pass = true;
+                // (s_save is written again only after the next batch has passed
+                // four more barriers, so every thread reads this value)
+                if (s_save) {
+                    // the new running best's vectors, before the next batch
+                    // overwrites the batch arrays
+                    const int wl = s_wl;
+                    for (int t = dt; t < j; t += DTHREADS) win_u[t] = con_u[wl * ldc + t];
+                    for (int i = dt; i < p; i += DTHREADS) win_x[i] = con_x[wl * p + i];
+                    if (dt == 0) {
+                        win_s[0] = con_v[wl];
+                        win_s[1] = con_r[wl];
+                        win_s[2] = con_ry[wl];
+                    }
+                    dsync();
+                }
             }
             // several contenders: release the FP32 group with the winner
             if (!lone) __syncthreads();
@@ -803,9 +781,12 @@ alc_bulk32_kernel(B32Params P) {
             // the partials of b = L^{-T} u* for the next row of L^{-1}, its
             // coordinates in the design
             const int wl = s_wl;
+            const bool saved = s_win_saved;  // the winner's vectors were kept from an earlier batch
+            const float2 *wu = saved ? win_u : con_u + wl * ldc, *wx = saved ? win_x : con_x + wl * p;
             if (!lone && dw == 0)
-                winner_scalars(ld2(con_v + wl), ld2(con_r + wl), ld2(con_ry + wl), j, fused, sel, best_row, lane, wv,
-                               zv, LT, ldl, s_il, s_qx, s_psi, s_mean, s_total);
+                winner_scalars(ld2(saved ? win_s : con_v + wl), ld2(saved ? win_s + 1 : con_r + wl),
+                               ld2(saved ? win_s + 2 : con_ry + wl), j, fused, sel, best_row, lane, wv, zv, LT, ldl,
+                               s_il, s_qx, s_psi, s_mean, s_total);
             if (dt == 32) {
                 // the ALC value (a lone contender's Delta is computed here) and
                 // the contender margin's error estimate
@@ -823,10 +804,10 @@ alc_bulk32_kernel(B32Params P) {
                 // longest chain is j / DWARPS; its partial covers s < t1
                 const int t0 = dw * j / DWARPS, t1 = (dw + 1) * j / DWARPS;
                 float2 *part = cpart + dw * ldc;
-                df_tri_upper(con_u + wl * ldc, LT, ldl, t0, t1, lane, part);
+                df_tri_upper(wu, LT, ldl, t0, t1, lane, part);
                 for (int s = t1 + lane; s < j; s += 32) part[s] = make_float2(0.f, 0.f);
             }
-            for (int i = dt; i < p; i += DTHREADS) xdd[i * ldx + j] = con_x[wl * p + i];
+            for (int i = dt; i < p; i += DTHREADS) xdd[i * ldx + j] = wx[i];
         }
         // (a double-float failure in the last step is seen here)
         __syncthreads();
@@ -859,7 +840,8 @@ alc_bulk32_kernel(B32Params P) {
 size_t b32_smem_bytes(int nmax, int p, int tmax, int npad) {
     const size_t ldl = b32_ldl(nmax), ldc = b32_ldc(nmax), ldx = b32_ldx(nmax);
     return 8 * ((size_t)nmax * ldl + EXP64_TABLE_SIZE + (size_t)p * ldx + (((size_t)p + 1) & ~(size_t)1) +
-                2 * ldx + 2 * (size_t)tmax * ldc + (size_t)WARPS * ldc + (size_t)tmax * p) +
+                2 * ldx + 2 * (size_t)tmax * ldc + (size_t)WARPS * ldc + (size_t)tmax * p + ldc +
+                (((size_t)p + 1) & ~(size_t)1)) +
            4 * 2 * (size_t)npad + 16;
 }
 

@@ -558,7 +558,7 @@ struct MleOut {
 
 __global__ void __launch_bounds__(GP_THREADS, 6)
 mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *counter, double *ws,
-           MleOut o) {
+           MleOut o, unsigned long long *work) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, ld = (nmax + 31) & ~31;
     GpShared S = carve(smem_raw, nmax, p);
@@ -566,6 +566,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
     GpWork W = work_for_block(ws, nmax, ld);
     __shared__ int s_loc, s_flag, s_chol;
     Blk b{(int)threadIdx.x, (int)threadIdx.x & 31, (int)threadIdx.x >> 5};
+    unsigned long long n_llik = 0, n_derivs = 0;  // evaluations x n^3 (thread 0's count)
     for (;;) {
         if (b.tid == 0) s_loc = atomicAdd(counter, 1);
         __syncthreads();
@@ -574,6 +575,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
         if (loc >= a.M) break;
         const int nm = a.n ? a.n[loc] : nmax;
         int st = load_design(a, loc, nm, dv, S.xd, S.y, &s_flag, b);
+        const unsigned long long n3 = (unsigned long long)nm * nm * nm;
         double l = CUDART_NAN, psi = 0.0;
         Derivs dr{CUDART_NAN, CUDART_NAN, CUDART_NAN, CUDART_NAN};
         int it = 0;
@@ -583,10 +585,12 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
             d = fmin(fmax(d, dmin), dmax);
             build_D(S.xd, nm, p, W.D, ld, b);
             build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
+            n_llik += n3;
             if (!llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &l, &psi, b)) {
                 st = LAGP_ENOTPD;
             } else {
                 dr = llik_derivs<true>(W, nm, ld, d, S.t3, S.a, psi, S.rd, S.t1, S.t2, b);
+                n_derivs += n3;
                 while (it < max_iter) {
                     it++;
                     double delta;
@@ -600,6 +604,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     for (int h = 0; h <= 20; h++) {
                         dn = fmin(fmax(d + delta, dmin), dmax);
                         build_K(W.D, nm, ld, dn, g, W.K, S.etab, b);
+                        n_llik += n3;
                         if (llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &ln, &psin, b) &&
                             (short_newton || ln >= l)) {
                             accepted = true;
@@ -611,6 +616,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                         // restore K, L, a at the current d
                         build_K(W.D, nm, ld, d, g, W.K, S.etab, b);
                         llik_value(W, nm, ld, S.y, S.t3, S.rd, S.ub, &s_chol, &l, &psi, b);
+                        n_llik += n3;
                         break;
                     }
                     const double step = fabs(dn - d);
@@ -618,6 +624,7 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
                     l = ln;
                     psi = psin;
                     dr = llik_derivs<true>(W, nm, ld, d, S.t3, S.a, psi, S.rd, S.t1, S.t2, b);
+                    n_derivs += n3;
                     if (step < 1e-10 * d) break;
                 }
             }
@@ -631,6 +638,10 @@ mle_kernel(GpArgs a, double *dv, double dmin, double dmax, int max_iter, int *co
             o.status[loc] = st;
         }
         __syncthreads();
+    }
+    if (b.tid == 0 && work) {
+        atomicAdd(work, n_llik);
+        atomicAdd(work + 1, n_derivs);
     }
 }
 
@@ -788,7 +799,11 @@ lagp_status launch_mle(lagp_ctx *ctx, const GpArgs &a, double *d, double dmin, d
     GpLaunch L;
     LAGP_TRY(prepare(ctx, a, mle_kernel, L));
     MleOut o{llik, dllik, d2llik, iters, status};
-    mle_kernel<<<L.grid, GP_THREADS, L.smem, ctx->stream>>>(a, d, dmin, dmax, max_iter, L.counter, L.ws, o);
+    int *ac = nullptr;
+    unsigned long long *aw = nullptr;
+    LAGP_TRY(alc_counters(ctx, &ac, &aw));  // (the MLE's words follow the ALC's)
+    mle_kernel<<<L.grid, GP_THREADS, L.smem, ctx->stream>>>(a, d, dmin, dmax, max_iter, L.counter, L.ws, o,
+                                                            aw + 8);
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
     return LAGP_OK;

@@ -56,7 +56,8 @@ lagp_status alc_counters(lagp_ctx *ctx, int **counter, unsigned long long **work
     *counter = reinterpret_cast<int *>(base);
     *work = reinterpret_cast<unsigned long long *>(base + 128);
     if (!ctx->work_zeroed) {
-        LAGP_CUDA(ctx, cudaMemsetAsync(*work, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        // the ALC words (offset 128) and the MLE words (offset 192)
+        LAGP_CUDA(ctx, cudaMemsetAsync(*work, 0, 128, ctx->stream));
         ctx->work_zeroed = true;
     }
     return LAGP_OK;
@@ -151,6 +152,21 @@ lagp_status lagp_alc_work(lagp_ctx *ctx, uint64_t *out) {
     LAGP_CUDA(ctx, cudaMemsetAsync(work, 0, sizeof h, ctx->stream));
     LAGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < 4; i++) out[i] = h[i];
+    return LAGP_OK;
+}
+
+lagp_status lagp_mle_work(lagp_ctx *ctx, uint64_t *out) {
+    if (!ctx || !out) return LAGP_EINVAL;
+    ctx->err.clear();
+    LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
+    int *counter = nullptr;
+    unsigned long long *work = nullptr;
+    LAGP_TRY(alc_counters(ctx, &counter, &work));
+    unsigned long long h[2] = {0, 0};
+    LAGP_CUDA(ctx, cudaMemcpyAsync(h, work + 8, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    LAGP_CUDA(ctx, cudaMemsetAsync(work + 8, 0, sizeof h, ctx->stream));
+    LAGP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2; i++) out[i] = h[i];
     return LAGP_OK;
 }
 

@@ -51,7 +51,8 @@ std::string alc_shape_key(const char *kernel, int cpt, int nmax, int p, bool fus
 int alc_ctas_per_sm(lagp_ctx *ctx, const std::string &key, int default_cps);
 
 // The persistent kernels' work counter (offset 0) and the ALC work counters
-// (4 x uint64 at offset 128) of the WS_ALC_COUNTER slot.
+// (4 x uint64 at offset 128; the MLE's 2 x uint64 follow at offset 192) of
+// the WS_ALC_COUNTER slot.
 lagp_status alc_counters(lagp_ctx *ctx, int **counter, unsigned long long **work);
 
 // status helpers (lagp_api.cu)

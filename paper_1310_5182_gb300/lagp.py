@@ -73,6 +73,7 @@ def _load():
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     lib.lagp_alc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lagp_mle_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
     lib.lagp_alc_eval.argtypes = [P, P, I64, I32, ctypes.c_int, P, P, I32, P, I64, D, D, P, P]
     lib.lagp_scale_inputs.argtypes = [P, P, I64, I32, ctypes.c_int, P, P]
     lib.lagp_exp64_check.argtypes = [P, P, I64, P, P]
@@ -84,7 +85,7 @@ def _load():
               "lagp_knn", "lagp_alc_select", "lagp_alc_predict", "lagp_predict", "lagp_predict_noalloc",
               "lagp_mle_step",
               "lagp_predict_grad", "lagp_autotune",
-              "lagp_agp", "lagp_alc_work", "lagp_exp64_check", "lagp_df_check", "lagp_alc_eval",
+              "lagp_agp", "lagp_alc_work", "lagp_mle_work", "lagp_exp64_check", "lagp_df_check", "lagp_alc_eval",
               "lagp_scale_inputs", "lagp_knn_tc_dist", "lagp_knn_stats", "lagp_knn_tc_stall"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
@@ -228,6 +229,15 @@ def alc_work(device=None) -> dict:
     _check(_lib.lagp_alc_work(ctx, out), ctx, "lagp_alc_work")
     return dict(locations=int(out[0]), rescored=int(out[1]), rescored_j=int(out[2]),
                 rescored_j2=int(out[3]))
+
+
+def mle_work(device=None) -> dict:
+    """Newton MLE work counters since the last read (then reset): the sums of
+    n^3 over likelihood evaluations and over derivative evaluations."""
+    ctx = context(device)
+    out = (ctypes.c_uint64 * 2)()
+    _check(_lib.lagp_mle_work(ctx, out), ctx, "lagp_mle_work")
+    return dict(llik_n3=int(out[0]), derivs_n3=int(out[1]))
 
 
 def exp64_check(a: torch.Tensor):

@@ -486,37 +486,84 @@ def test_borehole_full_size_sampled(L, O, prec):
                w.Y, w.Xref[samp][same], ref["sel"][same], np.full(len(same), 50), 2.0, 1e-6)
 
 
-def test_borehole_1m_uneven_mle_full_size_sampled(L, O):
-    """The 1M-point uneven configuration (N=1,000,000 FP32, M=20,000,
-    n ~ U{30..100}, N' ~ U{500..2000}, Newton MLE of d from 2.0 within
-    [1e-3, 20], <= 10 iterations) run whole on the GPU as the benchmark runs
-    it; sampled locations are checked stage by stage against the oracle on
-    the GPU's own inputs to each stage."""
-    w = W.c3_borehole_1m_uneven()
+def retried_queries(L, X, Xr, Npm, Np_t, n_retry):
+    """The reference locations that the kNN's exact retry recomputed: whether
+    a location overflows its sampled threshold depends on it alone (the
+    sample stride follows N and N'_max), so bisecting the locations with
+    the retry counter of lagp_knn_stats finds them."""
+    found, todo = [], [(0, Xr.shape[0], n_retry)]
+    while todo:
+        lo, hi, r = todo.pop()
+        if r == 0:
+            continue
+        if hi - lo == 1:
+            found.append(lo)
+            continue
+        mid = (lo + hi) // 2
+        L.lagp_knn(X, Xr[lo:mid], Npm, Nprime=Np_t[lo:mid])
+        r_lo = L.knn_stats()["retried"]
+        todo += [(lo, mid, r_lo), (mid, hi, r - r_lo)]
+    return sorted(found)
+
+
+def full_size_sampled(L, O, w, n_samp=8, seed=41, max_div=2):
+    """One configuration run whole on the GPU as the benchmark runs it (kNN,
+    FP32-bulk ALC search, Newton MLE of d, prediction); sampled locations,
+    and every location the kNN's exact retry recomputed, are checked stage
+    by stage against the oracle on the GPU's own inputs to each stage."""
     X, Y, Xr = dev(w.X), dev(w.Y), dev(w.Xref)
     n_t, Np_t = dev(w.n), dev(w.Np)
     Npm, nmax = int(w.Np.max()), int(w.n.max())
     idx, st = L.lagp_knn(X, Xr, Npm, Nprime=Np_t)
+    n_retry = L.knn_stats()["retried"]
     s = L.lagp_alc_select(X, Xr, idx, w.n0, n_t, w.d, w.g, prec="f32bulk", Nprime=Np_t, n_max=nmax)
     m = L.lagp_mle_step(X, Y, s["sel"], n_t, w.d, w.g, *w.mle)
     pr = L.lagp_predict(X, Y, Xr, s["sel"], n_t, m["d"], w.g)
     torch.cuda.synchronize()
     for t in (st, s["status"], m["status"], pr["status"]):
         assert (t.cpu().numpy() == 0).all()
-    samp = np.random.default_rng(41).choice(w.M, 8, replace=False)
+    idx_h, sel_h, d_h = idx.cpu().numpy(), s["sel"].cpu().numpy(), m["d"].cpu().numpy()
+    mean_h, s2_h = pr["mean"].cpu().numpy(), pr["s2"].cpu().numpy()
+    retried = retried_queries(L, X, Xr, Npm, Np_t, n_retry) if n_retry else []
+    assert len(retried) == n_retry
+    samp = np.union1d(np.random.default_rng(seed).choice(w.M, n_samp, replace=False),
+                      np.asarray(retried, dtype=np.int64))
     n_s, Np_s = w.n[samp], w.Np[samp]
     ref_idx = O.knn(w.X, w.Xref[samp], Npm, Np_s)
-    assert np.array_equal(idx.cpu().numpy()[samp], ref_idx)
+    assert np.array_equal(idx_h[samp], ref_idx)
     ref = O.alc_select(w.X, w.Xref[samp], ref_idx, w.n0, n_s, w.d, w.g, Np=Np_s, nmax=nmax, topk=4)
-    sel = s["sel"].cpu().numpy()[samp]
+    sel = sel_h[samp]
     div = compare_selection(sel, ref, n_s, w.n0, w.g)
-    assert len(div) <= 2
-    d_gpu = m["d"].cpu().numpy()[samp]
+    assert len(div) <= max_div
     ref_m = O.mle(w.X, w.Y, sel, n_s, w.d, w.g, *w.mle)
-    np.testing.assert_allclose(d_gpu, ref_m["d"], rtol=1e-6)
-    ref_p = O.predict(w.X, w.Y, w.Xref[samp], sel, n_s, d_gpu, w.g)
-    check_pred(pr["mean"].cpu().numpy()[samp], pr["s2"].cpu().numpy()[samp], ref_p, w.X, w.Y,
-               w.Xref[samp], sel, n_s, d_gpu, w.g)
+    np.testing.assert_allclose(d_h[samp], ref_m["d"], rtol=1e-6)
+    ref_p = O.predict(w.X, w.Y, w.Xref[samp], sel, n_s, d_h[samp], w.g)
+    check_pred(mean_h[samp], s2_h[samp], ref_p, w.X, w.Y, w.Xref[samp], sel, n_s, d_h[samp], w.g)
+    return n_retry
+
+
+def test_borehole_1m_uneven_mle_full_size_sampled(L, O):
+    """The 1M-point uneven configuration (N=1,000,000 FP32, M=20,000,
+    n ~ U{30..100}, N' ~ U{500..2000}, Newton MLE of d from 2.0 within
+    [1e-3, 20], <= 10 iterations), whole, against the oracle on samples."""
+    full_size_sampled(L, O, W.c3_borehole_1m_uneven())
+
+
+def test_slab3d_500k_grid_mle_full_size_sampled(L, O):
+    """The nonstationary 3-d configuration (Sec. 5.1's experiment on a
+    synthetic stand-in: N=500,000 FP32, the 60x60x56 grid of 201,600
+    reference locations, (n0, n, N') = (6, 60, 1500), Newton MLE of d),
+    whole, against the oracle on samples."""
+    full_size_sampled(L, O, W.c4_slab3d())
+
+
+def test_borehole_4m_mle_full_size_sampled(L, O):
+    """The 4M-point borehole configuration (Sec. 5.2's scale-out: N=4,000,000
+    FP32, M=100,000, (6, 50, 2000), Newton MLE of d), whole, against the
+    oracle on samples and on every location the kNN's exact retry
+    recomputed (the sampled threshold's largest stride, 64, applies here)."""
+    n_retry = full_size_sampled(L, O, W.c5_borehole_4m())
+    print(f"kNN exact retries: {n_retry}")
 
 
 # ------------------------------- one location, many candidates (Sec. 4.1)
