@@ -137,8 +137,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "ea5b35d9b9b5a733aa089959f175ecdf628ff94d0a26e2d9ace9ae7b9073cf42",
-               "dram_bytes_per_location": (4.330874e9 + 0.688441e9) / 3040}
+ALC_TRAFFIC = {"sha256": "e1289bfc546803a9533cd3ba41a70ef4cce160298191f0767ccc6a7cf8e3f9df",
+               "dram_bytes_per_location": (1.815380e9 + 0.786226e9) / 3040}
 
 
 def alc_source_hash():
