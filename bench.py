@@ -375,6 +375,32 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
             stages.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3]),
                            ev[3].elapsed_time(ev[4])])
     mw = L.mle_work(dev)
+    graph = None
+    if w.mle is not None:
+        # the same step captured once in a CUDA graph (per-location n and N'
+        # as device arrays; workspaces sized by the eager steps) and replayed
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gs):
+            gouts, _ = step()
+        gms = []
+        for _ in range(steps):
+            if flush is not None:
+                flush.zero_()
+            torch.cuda.synchronize(dev)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            g.replay()
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            gms.append(g0.elapsed_time(g1))
+        same = all(torch.equal(torch.nan_to_num(gouts[k], nan=-7.0), torch.nan_to_num(outs[k], nan=-7.0))
+                   for k in ("sel", "d", "mean", "s2"))
+        gm = statistics.mean(gms)
+        graph = {"ms_per_step": round(gm, 3), "value": w.M / (gm / 1e3), "unit": "predictions/s",
+                 "identical_to_eager": bool(same)}
+        del g, gouts
     ok = np.all([t.cpu().numpy() == 0 for t in sts], axis=0)
     outs = {k: v.cpu().numpy() for k, v in outs.items()}
     mean = outs["mean"]
@@ -400,6 +426,8 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
         res["mle_roofline"] = {"bound": "alu", "kernel": "mle_kernel", "unit": "TFLOP/s", "achieved": ach,
                                "peak": peak, "frac": ach / peak, "fp64_flops_per_launch": fl,
                                "peak_source": f"derived: FP64 FMA, {sms} SMs x 4 flop/cycle x 2070 MHz"}
+    if graph is not None:
+        res["cuda_graph"] = graph
     if oracle_S:
         res["vs_oracle"] = vs_oracle_leg(w, outs, oracle_S)[0]
     return res

@@ -96,6 +96,42 @@ def test_search_captured_in_cuda_graph(L, prec):
         assert torch.equal(out_g["s2"], eager["s2"])
 
 
+def test_uneven_mle_pipeline_captured_in_cuda_graph(L):
+    """The whole MLE pipeline of the batched uneven configuration (kNN ->
+    FP32-bulk search -> Newton MLE of d -> prediction, per-location n and N'
+    drawn as in the 1M-point workload, on a smaller design), captured once
+    and replayed twice: every output bitwise the eager calls'."""
+    w = W.borehole(seed=57, N=60_000, M=400, n_range=(30, 100), Np_range=(500, 2000), dtype=np.float32,
+                   mle=(1e-3, 20.0, 10))
+    dev = torch.device("cuda", 0)
+    X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
+    n_t, Np_t = torch.from_numpy(w.n).to(dev), torch.from_numpy(w.Np).to(dev)
+    Npm, nmax = int(w.Np.max()), int(w.n.max())
+
+    def pipeline():
+        idx, _ = L.lagp_knn(X, Xr, Npm, Nprime=Np_t)
+        s = L.lagp_alc_select(X, Xr, idx, w.n0, n_t, w.d, w.g, prec="f32bulk", Nprime=Np_t, n_max=nmax,
+                             want_alc=True)
+        m = L.lagp_mle_step(X, Y, s["sel"], n_t, w.d, w.g, *w.mle)
+        pr = L.lagp_predict(X, Y, Xr, s["sel"], n_t, m["d"], w.g)
+        return dict(idx=idx, sel=s["sel"], alc=s["alc"], d=m["d"], iters=m["iters"], mean=pr["mean"],
+                    s2=pr["s2"], st=torch.stack([s["status"], m["status"], pr["status"]]))
+
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        eager = pipeline()  # (workspaces sized outside the capture)
+    torch.cuda.synchronize()
+    assert (eager["st"] == 0).all()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        got = pipeline()
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        for k in eager:
+            assert torch.equal(torch.nan_to_num(got[k], nan=-7.0), torch.nan_to_num(eager[k], nan=-7.0)), k
+
+
 def test_autotune_picks_a_grid_and_results_do_not_depend_on_it(L):
     """The autotuner times every admissible resident-CTA count; the designs
     (one persistent CTA per location at a time) must not depend on it."""
