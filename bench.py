@@ -355,6 +355,12 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
         return (dict(idx=idx, sel=s["sel"], d=m["d"], mean=pr["mean"], s2=pr["s2"]),
                 [st, s["status"], m["status"], pr["status"]])
 
+    # the project's autotuner: resident CTAs per SM and (FP32-bulk) re-score
+    # batch for this shape, on a sample, outside the timed region
+    idx0, _ = L.lagp_knn(X, Xr, Npm, Nprime=Np_t)
+    tuned = L.lagp_autotune(X, Xr, idx0, w.n0, n_t, w.d, w.g, prec=prec, Y=Y if w.mle is None else None,
+                            Nprime=Np_t, n_max=nmax)
+    del idx0
     for _ in range(warmup):
         step()
     times, stages = [], []
@@ -408,7 +414,7 @@ def config_leg(L, dev, w, prec, steps, warmup, flush=None, oracle_S=0):
     res = {"value": w.M / (ms / 1e3), "unit": "predictions/s", "ms_per_step": round(ms, 3), "steps": steps,
            "M": w.M, "N": w.N, "p": w.p, "n": [int(w.n.min()), int(w.n.max())],
            "Nprime": [int(w.Np.min()), int(w.Np.max())], "dtype": str(w.X.dtype), "prec": prec,
-           "mle": list(w.mle) if w.mle else None, "status_ok_frac": float(ok.mean()),
+           "mle": list(w.mle) if w.mle else None, "alc_tuned": tuned, "status_ok_frac": float(ok.mean()),
            "rmse_vs_truth": float(np.sqrt(np.mean((mean[ok] - w.truth[ok]) ** 2)))}
     st_ms = np.mean(np.array(stages), axis=0)
     if w.mle is None:
@@ -584,7 +590,7 @@ def run_ours(args, rank, world, local_rank):
     # the project's autotuner picks the resident CTAs per SM of the ALC kernel
     # for this problem shape (outside the timed region)
     idx0, _ = L.lagp_knn(X, Xr, Np)
-    tuned = L.lagp_autotune(X, Xr, idx0, n0, n, d, g, prec=args.prec, Y=Y)
+    tuned = L.lagp_autotune(X, Xr, idx0, n0, n, d, g, prec=args.prec, Y=Y)  # dict: the two choices
     for _ in range(args.warmup):
         step(args.prec)
     barrier()
@@ -792,7 +798,7 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": w.N, "M_per_gpu": M, "p": w.p, "n0": n0, "n": n,
-                   "Nprime": Np, "d": d, "g": g, "prec": args.prec, "alc_ctas_per_sm": tuned,
+                   "Nprime": Np, "d": d, "g": g, "prec": args.prec, "alc_tuned": tuned,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -86,9 +86,11 @@ typedef struct {
     int32_t ctas_per_sm;    /* resident CTAs per SM of the ALC kernels */
     int32_t block_threads;  /* threads per CTA of the ALC kernels */
     int32_t rescore_max;    /* F32BULK: contenders re-scored together in one
-                               batch, 1..32, used up to 8 (default 8); more
-                               contenders take further batches, none is
-                               dropped */
+                               batch, 1..32, used up to 8; 0 = automatic (the
+                               autotuner's choice for the shape, else 8).
+                               More contenders take further batches, none is
+                               dropped.  (F64SCHUR: the contenders re-scored,
+                               0 = 8.) */
     double rescore_rel;     /* F32BULK: cap of the contender margin (default
                                0.5).  A candidate is a contender when its FP32
                                score is within the margin of the FP32 maximum;
@@ -167,17 +169,20 @@ lagp_status lagp_df_check(lagp_ctx *ctx, const double *a, int64_t n, float *spli
 
 /* Autotuner.  Times the ALC search (a2..a6, or a2..a7 when Y is not NULL) on
  * a sample of the given problem (its first min(M, 16 x SMs) locations) for
- * every admissible number of resident CTAs per SM of the persistent kernel,
- * and records the fastest for problems of this shape (precision, N'
- * capacity, n_max, p, with or without prediction) on this context; later
- * calls with tuning.ctas_per_sm == 0 use it.  Synchronises the stream.
- * Arguments as lagp_alc_predict; *best_ctas_per_sm (may be NULL) receives the
- * choice. */
+ * every admissible number of resident CTAs per SM of the persistent kernel
+ * and, for F32BULK with tuning.rescore_max == 0, for double-float re-score
+ * batches of 8 and 4 contenders, and records the fastest for problems of
+ * this shape (precision, N' capacity, n_max, p, with or without prediction)
+ * on this context; later calls with tuning.ctas_per_sm == 0 (and
+ * rescore_max == 0) use it.  Results do not depend on either choice.
+ * Synchronises the stream.  Arguments as lagp_alc_predict;
+ * *best_ctas_per_sm and *best_rescore_max (either may be NULL) receive the
+ * choices. */
 lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, int32_t p, lagp_dtype dtype,
                           const void *Xref, int64_t M, const int32_t *idx, const int32_t *Nprime,
                           int32_t Nprime_max, int32_t n0, const int32_t *n, int32_t n_max,
                           const double *d, double g, lagp_precision prec, const void *Y,
-                          int32_t *best_ctas_per_sm);
+                          int32_t *best_ctas_per_sm, int32_t *best_rescore_max);
 
 /* ---------------------------------------------------------------- a1: kNN
  * Exact N'-nearest-neighbour candidate sets (Sec. 3.1: the ALC search is

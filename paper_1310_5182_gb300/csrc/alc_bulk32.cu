@@ -571,10 +571,13 @@ alc_bulk32_kernel(B32Params P) {
                 }
                 dsync();
                 // ---- R1: k_j(x_c) (t < j) and K(x_c, x) (t = j) in double-float;
-                // each squared distance split over G lanes (G in 1, 2, 4)
+                // each squared distance split over G lanes (G in 1, 2, 4).  G,
+                // and R2's layout below, follow the step's contender count, not
+                // the batch's, so that a contender's arithmetic (and every
+                // result) is the same for any batch size
                 {
-                    const int jp = j + 1, pairs = ncon * jp;
-                    const int G = pairs * 4 <= DTHREADS ? 4 : (pairs * 2 <= DTHREADS ? 2 : 1);
+                    const int jp = j + 1, pairs = ncon * jp, tpairs = min(total, TMAX_CAP) * jp;
+                    const int G = tpairs * 4 <= DTHREADS ? 4 : (tpairs * 2 <= DTHREADS ? 2 : 1);
                     const int gi = dt & (G - 1), per = DTHREADS / G;
                     for (int base = 0; base < pairs; base += per) {
                         const int pr = base + dt / G;
@@ -607,9 +610,9 @@ alc_bulk32_kernel(B32Params P) {
                 // each contender's rows split over wpc warps; with more, one
                 // thread per (contender, t) over the whole group (two
                 // accumulation chains), so that the chains are j/2 long
-                const int wpc = ncon == 1 ? 4 : (ncon == 2 ? 2 : 1);
+                const int wpc = total == 1 ? 4 : (total == 2 ? 2 : 1);
                 if (j > 0) {
-                    if (ncon >= 3) {
+                    if (total >= 3) {
                         for (int e = dt; e < ncon * j; e += DTHREADS) {
                             const int w = e / j, t = e - w * j;
                             const float2 *kc = con_k + w * ldc;
@@ -849,8 +852,8 @@ template <int CPT>
 lagp_status launch_b32(lagp_ctx *ctx, const AlcArgs &a) {
     constexpr int NPAD = FTHREADS * CPT;
     cudaStream_t st = ctx->stream;
-    int tmax = ctx->tuning.rescore_max > 0 ? ctx->tuning.rescore_max : 8;
-    tmax = std::max(1, std::min(tmax, TMAX_CAP));
+    const std::string key = alc_shape_key("alc_f32", CPT, a.nmax, a.p, a.mean != nullptr);
+    const int tmax = std::max(1, std::min(alc_rescore_batch(ctx, key), TMAX_CAP));
     auto kern = alc_bulk32_kernel<CPT>;
     const size_t smem = b32_smem_bytes(a.nmax, a.p, tmax, NPAD);
     if (smem > ctx->smem_optin)
@@ -858,8 +861,7 @@ lagp_status launch_b32(lagp_ctx *ctx, const AlcArgs &a) {
     LAGP_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
     LAGP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem));
-    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key("alc_f32", CPT, a.nmax, a.p, a.mean != nullptr),
-                                 b32_min_blocks<CPT>());
+    int per_sm = alc_ctas_per_sm(ctx, key, b32_min_blocks<CPT>());
     if (occ > 0 && per_sm > occ) per_sm = occ;
     int64_t grid = (int64_t)ctx->num_sms * std::max(1, per_sm);
     if (grid > a.M) grid = a.M;

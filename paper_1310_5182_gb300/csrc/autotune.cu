@@ -1,6 +1,7 @@
 // Autotuner for the persistent ALC kernels: times the search on a sample of
 // the caller's problem for every admissible count of resident CTAs per SM
-// and records the fastest for that problem shape on the context.
+// (and, for the FP32-bulk kernel, two double-float re-score batch sizes) and
+// records the fastest for that problem shape on the context.
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -15,10 +16,18 @@ std::string alc_shape_key(const char *kernel, int cpt, int nmax, int p, bool fus
 }
 
 int alc_ctas_per_sm(lagp_ctx *ctx, const std::string &key, int default_cps) {
+    ctx->last_alc_key = key;
     if (ctx->tune_override > 0) return ctx->tune_override;
     if (ctx->tuning.ctas_per_sm > 0) return ctx->tuning.ctas_per_sm;
     auto it = ctx->tuned_ctas.find(key);
     return it != ctx->tuned_ctas.end() ? it->second : default_cps;
+}
+
+int alc_rescore_batch(lagp_ctx *ctx, const std::string &key) {
+    if (ctx->tune_tmax_override > 0) return ctx->tune_tmax_override;
+    if (ctx->tuning.rescore_max > 0) return ctx->tuning.rescore_max;
+    auto it = ctx->tuned_tmax.find(key);
+    return it != ctx->tuned_tmax.end() ? it->second : 8;
 }
 
 extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, int32_t p,
@@ -26,7 +35,7 @@ extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, in
                                      const int32_t *idx, const int32_t *Nprime, int32_t Nprime_max,
                                      int32_t n0, const int32_t *n, int32_t n_max, const double *d,
                                      double g, lagp_precision prec, const void *Y,
-                                     int32_t *best_ctas_per_sm) {
+                                     int32_t *best_ctas_per_sm, int32_t *best_rescore_max) {
     if (!ctx) return LAGP_EINVAL;
     if (M <= 0) return lagp_fail(ctx, LAGP_EINVAL, "lagp_autotune: M must be > 0");
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -45,11 +54,17 @@ extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, in
     LAGP_CUDA(ctx, cudaEventCreate(&e0));
     LAGP_CUDA(ctx, cudaEventCreate(&e1));
     const int max_cps = prec == LAGP_PREC_F32BULK ? 4 : 3;
+    // the FP32-bulk kernel's re-score batch too (unless the user fixed it)
+    const bool tune_b = prec == LAGP_PREC_F32BULK && ctx->tuning.rescore_max == 0;
+    const int batches[2] = {8, 4};
     float best_ms = 1e30f;
-    int best = 0;
+    int best = 0, best_b = 0;
+    std::string key;
     lagp_status rc = LAGP_OK;
-    for (int cps = 1; cps <= max_cps && rc == LAGP_OK; cps++) {
+    for (int trial = 0; trial < max_cps * (tune_b ? 2 : 1) && rc == LAGP_OK; trial++) {
+        const int cps = 1 + trial % max_cps, tb = tune_b ? batches[trial / max_cps] : 0;
         ctx->tune_override = cps;
+        ctx->tune_tmax_override = tb;
         float ms_sum = 0.f;
         for (int rep = 0; rep < 3 && rc == LAGP_OK; rep++) {
             cudaEventRecord(e0, ctx->stream);
@@ -70,21 +85,19 @@ extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, in
         if (rc == LAGP_OK && ms_sum < best_ms) {
             best_ms = ms_sum;
             best = cps;
+            best_b = tb;
         }
+        key = ctx->last_alc_key;  // the launcher's own key for this shape
     }
     ctx->tune_override = 0;
+    ctx->tune_tmax_override = 0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != LAGP_OK) return rc;
-    // record under the key the launcher will look up for this shape
-    const int need = (Nprime_max + 255) / 256;
-    const int cpt = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
-    const std::string key = prec == LAGP_PREC_F32BULK
-                                ? alc_shape_key("alc_f32", cpt, n_max, p, Y != nullptr)
-                                : prec == LAGP_PREC_F64SCHUR
-                                      ? alc_shape_key("alc_f64schur", cpt, n_max, p, Y != nullptr)
-                                      : alc_shape_key("alc_f64", 0, n_max, p, Y != nullptr);
+    // recorded under the key the launcher looked up during the trials
     ctx->tuned_ctas[key] = best;
+    if (tune_b) ctx->tuned_tmax[key] = best_b;
     if (best_ctas_per_sm) *best_ctas_per_sm = best;
+    if (best_rescore_max) *best_rescore_max = tune_b ? best_b : alc_rescore_batch(ctx, key);
     return LAGP_OK;
 }

@@ -130,7 +130,7 @@ lagp_status lagp_get_tuning(const lagp_ctx *ctx, lagp_tuning *out) {
 lagp_status lagp_set_tuning(lagp_ctx *ctx, const lagp_tuning *in) {
     if (!ctx || !in) return LAGP_EINVAL;
     if (in->ctas_per_sm < 0 || in->ctas_per_sm > 32 || in->block_threads < 0 ||
-        in->block_threads > 1024 || (in->block_threads % 32) != 0 || in->rescore_max < 1 ||
+        in->block_threads > 1024 || (in->block_threads % 32) != 0 || in->rescore_max < 0 ||
         in->rescore_max > 32 || !(in->rescore_rel >= 0.0) || !(in->rescore_rel < 1.0) ||
         in->knn_path < 0 || in->knn_path > 1)
         return lagp_fail(ctx, LAGP_EINVAL, "lagp_set_tuning: field out of range");

@@ -32,11 +32,14 @@ struct lagp_ctx {
     void *ws[WS_NSLOTS] = {};
     size_t ws_bytes[WS_NSLOTS] = {};
     std::string err;
-    lagp_tuning tuning = {0, 0, 8, 0.5, 0};
+    lagp_tuning tuning = {0, 0, 0, 0.5, 0};
     int64_t launches = 0;
     // autotuned resident CTAs per SM, keyed by the ALC problem shape
     std::map<std::string, int> tuned_ctas;
-    int tune_override = 0;  // set by the autotuner while it times a candidate
+    std::map<std::string, int> tuned_tmax;  // FP32-bulk re-score batch by shape
+    int tune_override = 0;       // set by the autotuner while it times a candidate
+    int tune_tmax_override = 0;  // (the batch size of the candidate)
+    std::string last_alc_key;    // shape key of the last ALC launch (the tuner records under it)
     bool work_zeroed = false;  // ALC work counters cleared once after allocation
     int64_t knn_last_M = 0;    // queries of the last lagp_knn call (for lagp_knn_stats)
     int knn_tc_stall = 0;      // test hook for the next tensor-core kNN pass (lagp_knn_tc_stall)
@@ -49,6 +52,9 @@ std::string alc_shape_key(const char *kernel, int cpt, int nmax, int p, bool fus
 // Resident CTAs per SM for an ALC launch: the autotuner's trial value, the
 // user's tuning, the tuned table, or the kernel's default.
 int alc_ctas_per_sm(lagp_ctx *ctx, const std::string &key, int default_cps);
+// The FP32-bulk re-score batch for a shape: the autotuner's candidate, the
+// user's tuning.rescore_max, the tuned choice, or 8.
+int alc_rescore_batch(lagp_ctx *ctx, const std::string &key);
 
 // The persistent kernels' work counter (offset 0) and the ALC work counters
 // (4 x uint64 at offset 128; the MLE's 2 x uint64 follow at offset 192) of

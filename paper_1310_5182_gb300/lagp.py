@@ -69,7 +69,7 @@ def _load():
     lib.lagp_predict_grad.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, P, D, P, P,
                                       P, P, P, P, P]
     lib.lagp_autotune.argtypes = [P, P, I64, I32, ctypes.c_int, P, I64, P, P, I32, I32, P, I32, P, D,
-                                  ctypes.c_int, P, P]
+                                  ctypes.c_int, P, P, P]
     lib.lagp_agp.argtypes = [P, P, P, I64, I32, ctypes.c_int, P, I64, P, I32, I32, P, I32, D, D,
                              ctypes.c_int, ctypes.c_int, D, D, I32, P, P, P, P, P]
     lib.lagp_alc_work.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
@@ -196,8 +196,10 @@ def set_tuning(device=None, **fields):
 
 
 def lagp_autotune(X, Xref, idx, n0, n, d, g, prec="f32bulk", Y=None, Nprime=None, n_max=None):
-    """Time the ALC search for each admissible resident-CTA count on a sample
-    of this problem and record the fastest on the context.  Returns it."""
+    """Time the ALC search on a sample of this problem for each admissible
+    resident-CTA count (and, for the FP32-bulk form, re-score batch size) and
+    record the fastest on the context.  Returns dict(ctas_per_sm,
+    rescore_max)."""
     ctx = context(X.device)
     N, p = X.shape
     M, Npmax = idx.shape
@@ -208,13 +210,14 @@ def lagp_autotune(X, Xref, idx, n0, n, d, g, prec="f32bulk", Y=None, Nprime=None
         n_max = int(nt.max().item()) if M else 1
     Npt, Npp = _opt_i32(Nprime, M, X.device, "Nprime", uniform=Npmax)
     dt = _per_loc_f64(d, M, X.device)
-    best = ctypes.c_int32(0)
+    best, best_b = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(_lib.lagp_autotune(ctx, _dev(X, "X"), N, p, _dtype_code(X), _dev(Xref, "Xref", X.dtype), M,
                               _dev(idx, "idx", torch.int32), Npp, Npmax, int(n0), npp, int(n_max),
                               _dev(dt, "d"), float(g), _PREC[prec],
-                              None if Y is None else _dev(Y, "Y", X.dtype), ctypes.byref(best)),
+                              None if Y is None else _dev(Y, "Y", X.dtype), ctypes.byref(best),
+                              ctypes.byref(best_b)),
            ctx, "lagp_autotune")
-    return int(best.value)
+    return {"ctas_per_sm": int(best.value), "rescore_max": int(best_b.value)}
 
 
 def launch_count(device=None) -> int:

@@ -133,15 +133,25 @@ def test_uneven_mle_pipeline_captured_in_cuda_graph(L):
 
 
 def test_autotune_picks_a_grid_and_results_do_not_depend_on_it(L):
-    """The autotuner times every admissible resident-CTA count; the designs
-    (one persistent CTA per location at a time) must not depend on it."""
-    w = W.borehole(seed=54, N=20_000, M=700, Np=300, n=25)
+    """The autotuner times every admissible resident-CTA count and re-score
+    batch; the designs and predictions must not depend on either (one
+    persistent CTA per location at a time; a contender's arithmetic follows
+    the step's contender count, not its batch), and the tuned choice must be
+    the one later calls use."""
+    w = W.toy2d(seed=54, N=20_000, M=700, Np=600, n=25)  # many contenders a step
     dev = torch.device("cuda", 0)
     X, Y, Xr = (torch.from_numpy(a).to(dev) for a in (w.X, w.Y, w.Xref))
-    idx, _ = L.lagp_knn(X, Xr, 300)
-    before = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g)
+    idx, _ = L.lagp_knn(X, Xr, 600)
+    before = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
     best = L.lagp_autotune(X, Xr, idx, 6, 25, w.d, w.g, prec="f32bulk", Y=Y)
-    assert 1 <= best <= 4
-    after = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g)
-    assert torch.equal(before["sel"], after["sel"])
-    assert torch.equal(before["mean"], after["mean"])
+    assert 1 <= best["ctas_per_sm"] <= 4 and best["rescore_max"] in (4, 8)
+    after = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
+    for k in ("sel", "mean", "s2", "alc"):
+        assert torch.equal(torch.nan_to_num(before[k]), torch.nan_to_num(after[k])), k
+    for cps in (1, 3):
+        for b in (1, 3, 8):
+            L.set_tuning(ctas_per_sm=cps, rescore_max=b)
+            out = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
+            for k in ("sel", "mean", "s2", "alc"):
+                assert torch.equal(torch.nan_to_num(before[k]), torch.nan_to_num(out[k])), (cps, b, k)
+    L.set_tuning(ctas_per_sm=0, rescore_max=0)
