@@ -302,11 +302,11 @@ def vs_oracle_leg(w, out, S, seed=7):
             j = int(np.flatnonzero(sel_g[r, :w.n[samp[r]]] != ref["sel"][r, :w.n[samp[r]]])[0])
             ti, tv = list(top["top_idx"][q, j]), top["top_val"][q, j]
             pick = int(sel_g[r, j])
-            gap = (tv[0] - tv[ti.index(pick)]) if pick in ti else np.inf
+            gap = (tv[0] - tv[ti.index(pick)]) if pick in ti else tv[0]  # (Delta >= 0)
             if gap <= max(1e-6 * abs(tv[0]), 16 * np.finfo(float).eps / w.g):
                 near += 1
             else:
-                gaps.append(float(gap / abs(tv[0])) if np.isfinite(gap) else None)
+                gaps.append(float(gap / abs(tv[0])))
         res["near_tie_divergences"] = near
         res["misses"] = len(gaps)
         res["miss_rel_gaps"] = gaps[:20]

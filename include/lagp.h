@@ -70,7 +70,12 @@ typedef enum { LAGP_F64 = 0, LAGP_F32 = 1 } lagp_dtype;
  *                    values.  No FP64 instruction is used (this GPU runs
  *                    FP64 at 1/64 of the FP32 rate); the double-float
  *                    Cholesky basis keeps the decisions' and predictions'
- *                    errors at ~sqrt(cond(K_j)) 2^-48.
+ *                    errors at ~sqrt(cond(K_j)) 2^-48.  A location where
+ *                    the FP32 screen breaks down (near-singular local
+ *                    matrices: no contender with m_j^{-1} > 0 in
+ *                    double-float) is redone in the same call by the
+ *                    LAGP_PREC_F64SCHUR form; status LAGP_ENOTPD only if
+ *                    that fails too.
  *  LAGP_PREC_F64SCHUR the same Schur-complement form with the candidate
  *                    state in FP64 (the incremental O(j) form of the
  *                    criterion, exact to FP64 rounding); the contenders

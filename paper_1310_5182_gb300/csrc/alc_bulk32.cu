@@ -832,6 +832,7 @@ alc_bulk32_kernel(B32Params P) {
                 a.df[loc] = ok ? (double)nm : CUDART_NAN;
             }
             a.status[loc] = status;
+            if (status == LAGP_ENOTPD && a.fail_count) atomicAdd(a.fail_count, 1);  // (the FP64 Schur retry)
             s_bad = LAGP_OK;
         }
         __syncthreads();

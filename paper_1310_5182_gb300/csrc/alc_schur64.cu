@@ -139,6 +139,8 @@ template <int CPT, typename T>
 __global__ void __launch_bounds__(F32_THREADS, bulk_min_blocks<T, CPT>())
 alc_bulk_kernel(F32Params P) {
     const AlcArgs &a = P.a;
+    // retry of the FP32-bulk form's failed locations: nothing to do
+    if (a.retry_count && *static_cast<const volatile int *>(a.retry_count) == 0) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.nmax, p = a.p, Npmax = a.Npmax, Npad = P.Npad, tmax = P.tmax;
     const bool fused = a.mean != nullptr;
@@ -197,6 +199,7 @@ alc_bulk_kernel(F32Params P) {
         const int64_t loc = s_loc;
         __syncthreads();
         if (loc >= a.M) break;
+        if (a.retry_count && a.status[loc] != LAGP_ENOTPD) continue;  // (retry: failed locations only)
 
         const int k = a.Np ? a.Np[loc] : Npmax;
         const int nm = a.n ? a.n[loc] : nmax;

@@ -118,6 +118,11 @@ struct AlcArgs {
     // all four null for a plain search
     const void *Y;
     double *mean, *s2, *df;
+    // FP32-bulk: counts the locations that end LAGP_ENOTPD (device int)
+    int *fail_count = nullptr;
+    // FP64 Schur retry of those: when set, only locations whose status is
+    // LAGP_ENOTPD are redone, and nothing at all when *retry_count is 0
+    const int *retry_count = nullptr;
 };
 
 lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a);

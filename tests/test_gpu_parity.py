@@ -91,8 +91,12 @@ def compare_selection(gpu_sel, ref, n_arr, n0, g, gap_rel=NEAR_TIE):
                 continue
             assert j >= n0, f"location {m}: seed {j} differs ({gs} vs {rs})"
             ti, tv = list(ref["top_idx"][m, j]), ref["top_val"][m, j]
-            assert gs in ti, f"location {m} step {j}: GPU pick {gs} not among oracle's best {ti}"
-            gap = tv[0] - tv[ti.index(gs)]
+            # a pick outside the oracle's best four has Delta >= 0 (Eq. dxy),
+            # so its gap is at most the best value: a near tie when that value
+            # is itself within the bar (every Delta under FP64's floor)
+            assert gs in ti or tv[0] <= max(gap_rel * abs(tv[0]), alc_atol(g)), \
+                f"location {m} step {j}: GPU pick {gs} not among oracle's best {ti}"
+            gap = tv[0] - tv[ti.index(gs)] if gs in ti else tv[0]
             assert gap <= max(gap_rel * abs(tv[0]), alc_atol(g)), \
                 f"location {m} step {j}: gap {gap / abs(tv[0]):.3e} (relative) is not a near tie"
             diverged.append(m)
@@ -214,19 +218,57 @@ def test_select_toy2d_full_config_f64schur(L, O):
     _select_case(L, O, W.c1_toy2d_fp64(), "f64schur", max_diverged=0.03)
 
 
-def test_select_toy2d_full_config_f32bulk_bound(L, O):
-    """The same workload through the FP32-bulk form.  Its criterion values
-    (Delta ~ 1e-7 late in the search) sit at the FP32 screen's resolution, so
-    the stated FP32-path bound here is: at most 5% of locations leave the
-    oracle's trajectory, each at a step whose oracle gap is below 1%, and the
-    out-of-sample RMSE matches the oracle's within 2%."""
+def test_select_toy2d_full_config_f32bulk(L, O):
+    """The same workload through the FP32-bulk form: every decision is taken
+    in double-float on the contenders of the FP32 screen, so it meets the
+    same near-tie rule as the FP64 forms; the out-of-sample RMSE matches the
+    oracle's within 2%."""
     w = W.c1_toy2d_fp64()
-    _select_case(L, O, w, "f32bulk", max_diverged=0.05, gap_rel=1e-2)
+    _select_case(L, O, w, "f32bulk", max_diverged=0.03)
     out = L.lagp_agp(w.X, w.Y, w.Xref, 6, 50, 1000, w.d, w.g, prec="f32bulk")
     ref = O.run_pipeline(w.X, w.Y, w.Xref, 6, 50, 1000, w.d, w.g)
     r32 = np.sqrt(np.mean((out["mean"] - w.truth) ** 2))
     r64 = np.sqrt(np.mean((ref["mean"] - w.truth) ** 2))
     assert abs(r32 - r64) <= 0.02 * r64
+
+
+@pytest.mark.parametrize("prec", ["f32bulk", "f64schur"])
+def test_search_ill_conditioned_clustered(L, O, prec):
+    """An ill-conditioned case: a design of tight clusters (1,000 clusters of
+    half-width 0.02, d = 0.05) with nugget g = 1e-7, local matrices with
+    cond(K) ~2e8.  Late in the search the ranking lies below what an FP64
+    evaluation in the K^{-1} basis resolves (there the oracle's own Delta
+    differs from a 50-digit evaluation by up to a few percent; at g = 1e-8
+    the oracle fails outright), so the near-tie rule is not the bar here.
+    The bar: every location succeeds (the FP32-bulk form's screen breaks
+    down on most of them and they are redone by the FP64 Schur form); the
+    local prediction (lagp_predict, a Cholesky factorisation of K_n) on each
+    returned design matches the oracle's prediction on that design within
+    the parity bar; the out-of-sample RMSE is within 10% of the oracle
+    pipeline's.  (The prediction the search carries along, grown by the
+    partitioned inverse in FP64, drifts here to ~1e-3 relative: each update
+    divides by m_j^{-1}, which has lost most of its digits; it is reported,
+    not checked against the bar.)"""
+    w = W.clustered2d()
+    idx = O.knn(w.X, w.Xref, 300)
+    s = L.lagp_alc_select(dev(w.X), dev(w.Xref), dev(idx), w.n0, 30, w.d, w.g, prec=prec)
+    torch.cuda.synchronize()
+    assert (s["status"].cpu().numpy() == 0).all()
+    pr = L.lagp_predict(dev(w.X), dev(w.Y), dev(w.Xref), s["sel"], 30, w.d, w.g)
+    torch.cuda.synchronize()
+    assert (pr["status"].cpu().numpy() == 0).all()
+    sel = s["sel"].cpu().numpy()
+    n_arr = np.full(w.M, 30)
+    ref_p = O.predict(w.X, w.Y, w.Xref, sel, n_arr, w.d, w.g)
+    mean = pr["mean"].cpu().numpy()
+    check_pred(mean, pr["s2"].cpu().numpy(), ref_p, w.X, w.Y, w.Xref, sel, n_arr, np.full(w.M, w.d), w.g)
+    ref = O.run_pipeline(w.X, w.Y, w.Xref, w.n0, 30, 300, w.d, w.g)
+    r_gpu = np.sqrt(np.mean((mean - w.truth) ** 2))
+    r_orc = np.sqrt(np.mean((ref["mean"] - w.truth) ** 2))
+    assert r_gpu <= 1.1 * r_orc
+    fused = L.lagp_alc_predict(dev(w.X), dev(w.Y), dev(w.Xref), dev(idx), w.n0, 30, w.d, w.g, prec=prec)
+    drift = np.abs(fused["mean"].cpu().numpy() - ref_p["mean"]) / np.abs(ref_p["mean"])
+    print(f"{prec}: fused prediction's largest relative drift {drift.max():.2e}")
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])

@@ -13,6 +13,8 @@ Workloads (the paper's own data is not available; these stand in for it):
   borehole   8-d borehole function of Sec. 5.2 on U[0,1]^8 inputs mapped to
              the physical ranges; y standardised by the design mean/sd.
              (The paper used Latin hypercube samples; i.i.d. uniform here.)
+  clustered2d  the 2-d toy surface on a design of tight clusters, nugget
+             1e-7 (local matrices with cond ~2e8).
   slab3d     3-d nonstationary surface, 70% of the design in the slab
              0.4 < x1 < 0.6, predicted on a 60 x 60 x 56 grid (a synthetic
              stand-in for the LGBB experiment of Sec. 5.1, whose data is not
@@ -86,6 +88,23 @@ def toy2d(seed=0, N=10_000, M=100, n0=6, n=50, Np=1000, d=0.5, g=1e-4, dtype=np.
     Xref = rng.uniform(-2.0, 2.0, size=(M, 2))
     Y = toy2d_f(X) + noise
     return Workload("toy2d", X.astype(dtype), Y.astype(dtype), Xref.astype(dtype), toy2d_f(Xref),
+                    n0, np.full(M, n, np.int32), np.full(M, Np, np.int32), d, g)
+
+
+def clustered2d(seed=5, N=20_000, M=40, clusters=1000, spread=0.02, n0=6, n=30, Np=300, d=0.05, g=1e-7,
+                dtype=np.float64):
+    """The 2-d toy surface on a design of tight clusters (each point within
+    `spread` of one of `clusters` uniform centres) with a tiny nugget: local
+    matrices with cond ~2e8, the hard case for a reduced-precision screen.
+    (At g = 1e-8 the FP64 method itself breaks down on this design: m_j^{-1}
+    of Eq. (piedef) evaluates <= 0 in FP64 at almost every location.)"""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(-2.0, 2.0, size=(clusters, 2))
+    X = centres[rng.integers(0, clusters, N)] + rng.uniform(-spread, spread, size=(N, 2))
+    noise = rng.normal(0.0, 0.001, size=N)
+    Xref = rng.uniform(-2.0, 2.0, size=(M, 2))
+    Y = toy2d_f(X) + noise
+    return Workload("clustered2d", X.astype(dtype), Y.astype(dtype), Xref.astype(dtype), toy2d_f(Xref),
                     n0, np.full(M, n, np.int32), np.full(M, Np, np.int32), d, g)
 
 
