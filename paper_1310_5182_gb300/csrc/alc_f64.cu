@@ -15,6 +15,20 @@
 // then a block argmax (ties to the lower design row) and the partitioned
 // inverse update of Sec. 2.2.  GB300 runs FP64 at 1/62 of the FP32 rate, so
 // this form is bound by the FP64 pipe; it is the plain reference form.
+//
+// Few locations (at least two resident CTAs a location, as on the
+// 100-location 2-d toy): one location per thread-block cluster of CS CTAs
+// instead (CS up to 4, not necessarily a power of two).  CTA r of the
+// cluster scores, and appends panel columns for, the candidates c with
+// c mod CS = r; each step the CTAs exchange their best through distributed
+// shared memory (one cluster barrier a step, the records double-buffered by
+// the step's parity) and every CTA applies the same partitioned-inverse
+// update to its own copy of K^{-1}, reading the winner's panel row from its
+// owner's global panel after the barrier: the copies stay identical bit for
+// bit, and so do the results whatever CS is.
+#include <algorithm>
+
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "device_util.cuh"
@@ -32,6 +46,7 @@ struct F64Shared {
     double *yd;      // nmax: responses of the design (fused prediction)
     double *alpha;   // nmax: K^{-1} Y_j (fused prediction)
     double *bstar;   // nmax: K^{-1} k*
+    double *part;    // 4 x ld: partial sums of K^{-1} k*
     double *xd;      // nmax x p: design coordinates
     double *xq;      // p: reference location
     unsigned char *chosen;  // Npmax
@@ -83,6 +98,10 @@ __device__ __forceinline__ double kern64(const double *a, const void *X, int64_t
     return exp(-s / d);
 }
 
+namespace cg = cooperative_groups;
+
+// CL: one location per cluster (candidates split over its CTAs)
+template <bool CL>
 __global__ void __launch_bounds__(F64_THREADS)
 alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_ws,
                double *__restrict__ kappa_ws) {
@@ -95,24 +114,39 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
     S.yd = S.kx + ld;
     S.alpha = S.yd + ld;
     S.bstar = S.alpha + ld;
-    S.xd = S.bstar + nmax;
+    S.part = S.bstar + nmax;
+    S.xd = S.part + 4 * (size_t)ld;
     S.xq = S.xd + (size_t)nmax * p;
     S.chosen = reinterpret_cast<unsigned char *>(S.xq + p);
     __shared__ int s_loc, s_bad, s_cstar;
     __shared__ double w_v[F64_WARPS];
     __shared__ int w_row[F64_WARPS], w_slot[F64_WARPS];
     __shared__ double s_delta, s_mu, s_ry, s_cx, s_psi, s_qx, s_ystar;
+    // the cluster's exchange of the step's best (by the step's parity)
+    __shared__ double x_v[2];
+    __shared__ int x_row[2], x_slot[2], x_bad[2];
     const bool fused = a.mean != nullptr;
 
     double *panel = panel_ws + (size_t)blockIdx.x * Npmax * nmax;  // [c][i], ld nmax
     double *kappa = kappa_ws + (size_t)blockIdx.x * Npmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // cluster rank and size (1 and 0 without clusters); candidates c with
+    // c mod CS = rank are this CTA's
+    const int CS = CL ? (int)cg::this_cluster().num_blocks() : 1;
+    const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
+    int64_t next_loc = CL ? blockIdx.x / CS : 0;
 
     for (;;) {
-        if (tid == 0) s_loc = atomicAdd(counter, 1);
-        __syncthreads();
-        const int64_t loc = s_loc;
-        __syncthreads();
+        int64_t loc;
+        if constexpr (CL) {
+            loc = next_loc;  // a static share of the locations per cluster
+            next_loc += gridDim.x / CS;
+        } else {
+            if (tid == 0) s_loc = atomicAdd(counter, 1);
+            __syncthreads();
+            loc = s_loc;
+            __syncthreads();
+        }
         if (loc >= a.M) break;
 
         const int k = a.Np ? a.Np[loc] : Npmax;
@@ -132,16 +166,19 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                 if (r < 0 || r >= a.N) s_bad = LAGP_EINVAL;
             }
         __syncthreads();
-        for (int t = tid; t < nmax; t += F64_THREADS) {
-            sel[t] = -1;
-            if (alc) alc[t] = CUDART_NAN;
-        }
+        // (outputs: the cluster's rank 0 alone writes them)
+        if (rank == 0)
+            for (int t = tid; t < nmax; t += F64_THREADS) {
+                sel[t] = -1;
+                if (alc) alc[t] = CUDART_NAN;
+            }
         if (s_bad != LAGP_OK) {
-            if (tid == 0) {
+            if (tid == 0 && rank == 0) {
                 a.status[loc] = s_bad;
                 if (fused) a.mean[loc] = a.s2[loc] = a.df[loc] = CUDART_NAN;
             }
-            continue;  // next location (loop head synchronises)
+            __syncthreads();
+            continue;  // next location
         }
 
         // reference location, chosen flags, K(x_c, x) for every candidate
@@ -158,10 +195,13 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
             double delta = CUDART_NAN;
             if (j < a.n0) {
                 cstar = j;  // Fig. 1 step 2(a): the nearest neighbours, in order
+                // (the owner's panel row of the seed is read after the barrier)
+                if constexpr (CL) cg::this_cluster().sync();
             } else {
-                // ---- score every unchosen candidate, one warp per candidate
+                // ---- score every unchosen candidate (this CTA's share), one
+                // warp per candidate
                 ArgBest best{0.0, -1, -1};
-                for (int c = warp; c < k; c += F64_WARPS) {
+                for (int c = rank + CS * warp; c < k; c += CS * F64_WARPS) {
                     if (S.chosen[c]) continue;
                     const double *prow = panel + (size_t)c * nmax;
                     double quad, kxb;
@@ -192,7 +232,34 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                         if (better(w_v[w], w_row[w], b0.v, b0.row)) b0 = ArgBest{w_v[w], w_row[w], w_slot[w]};
                     s_cstar = b0.slot;
                     s_delta = b0.v;
-                    if (b0.slot < 0) s_bad = LAGP_ENOTPD;
+                    if constexpr (CL) {
+                        x_v[j & 1] = b0.v;
+                        x_row[j & 1] = b0.row;
+                        x_slot[j & 1] = b0.slot;
+                        x_bad[j & 1] = s_bad;
+                    } else if (b0.slot < 0) {
+                        s_bad = LAGP_ENOTPD;
+                    }
+                }
+                if constexpr (CL) {
+                    // the cluster's best (ties to the lower row), the same in every CTA
+                    cg::cluster_group cl = cg::this_cluster();
+                    cl.sync();
+                    if (tid == 0) {
+                        ArgBest b0{-CUDART_INF, INT32_MAX, -1};
+                        int bad = LAGP_OK;
+                        for (int r = 0; r < CS; r++) {
+                            const double v = *cl.map_shared_rank(&x_v[j & 1], r);
+                            const int row = *cl.map_shared_rank(&x_row[j & 1], r);
+                            const int slot = *cl.map_shared_rank(&x_slot[j & 1], r);
+                            const int rb = *cl.map_shared_rank(&x_bad[j & 1], r);
+                            if (rb != LAGP_OK) bad = rb;
+                            if (slot >= 0 && (b0.slot < 0 || better(v, row, b0.v, b0.row))) b0 = ArgBest{v, row, slot};
+                        }
+                        s_cstar = b0.slot;
+                        s_delta = b0.v;
+                        s_bad = bad != LAGP_OK ? bad : (b0.slot < 0 ? LAGP_ENOTPD : LAGP_OK);
+                    }
                 }
                 __syncthreads();
                 if (s_bad != LAGP_OK) {
@@ -202,12 +269,32 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                 cstar = s_cstar;
                 delta = s_delta;
             }
-            // ---- partitioned inverse update with x* = candidate cstar (Sec. 2.2)
-            const double *kst = panel + (size_t)cstar * nmax;
-            for (int t = tid; t < j; t += F64_THREADS) {
-                double s = 0.0;
-                for (int kk = 0; kk < j; kk++) s = fma(S.Kinv[(size_t)kk * ld + t], kst[kk], s);
-                S.bstar[t] = s;
+            // ---- partitioned inverse update with x* = candidate cstar (Sec. 2.2);
+            // its panel row from the CTA that owns it
+            const double *kst =
+                (CL ? panel_ws + (size_t)(blockIdx.x - rank + cstar % CS) * Npmax * nmax : panel) +
+                (size_t)cstar * nmax;
+            // b* = K^{-1} k*: each output summed by QS threads over a share of
+            // the rows, two chains each (short dependent FP64 chains)
+            {
+                const int QS = j * 4 <= F64_THREADS ? 4 : (j * 2 <= F64_THREADS ? 2 : 1);
+                for (int e = tid; e < j * QS; e += F64_THREADS) {
+                    const int t = e % j, q = e / j, k0 = q * j / QS, k1 = (q + 1) * j / QS;
+                    double s0 = 0.0, s1 = 0.0;
+                    int kk = k0;
+                    for (; kk + 1 < k1; kk += 2) {
+                        s0 = fma(S.Kinv[(size_t)kk * ld + t], kst[kk], s0);
+                        s1 = fma(S.Kinv[(size_t)(kk + 1) * ld + t], kst[kk + 1], s1);
+                    }
+                    if (kk < k1) s0 = fma(S.Kinv[(size_t)kk * ld + t], kst[kk], s0);
+                    S.part[(size_t)q * ld + t] = s0 + s1;
+                }
+                __syncthreads();
+                for (int t = tid; t < j; t += F64_THREADS) {
+                    double s = S.part[t];
+                    for (int q = 1; q < QS; q++) s += S.part[(size_t)q * ld + t];
+                    S.bstar[t] = s;
+                }
             }
             __syncthreads();
             if (tid < 32) {
@@ -272,8 +359,10 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                 S.Kinv[(size_t)j * ld + j] = mu;
                 S.kx[j] = kappa[cstar];
                 S.chosen[cstar] = 1;
-                sel[j] = cands[cstar];
-                if (alc) alc[j] = delta;
+                if (rank == 0) {
+                    sel[j] = cands[cstar];
+                    if (alc) alc[j] = delta;
+                }
             }
             for (int i = tid; i < p; i += F64_THREADS)
                 S.xd[(size_t)j * p + i] = load_coord64(a.X, cands[cstar], p, i, a.dtype);
@@ -281,12 +370,12 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
             // ---- append panel column j: K(x_c, x*) for every candidate (no nugget)
             if (j + 1 < nm) {
                 const double *xs = S.xd + (size_t)j * p;
-                for (int c = tid; c < k; c += F64_THREADS)
+                for (int c = rank + CS * tid; c < k; c += CS * F64_THREADS)
                     panel[(size_t)c * nmax + j] = kern64(xs, a.X, cands[c], p, a.dtype, d);
             }
             __syncthreads();
         }
-        if (status != LAGP_OK) {
+        if (status != LAGP_OK && rank == 0) {
             for (int t = tid; t < nmax; t += F64_THREADS) {
                 sel[t] = -1;
                 if (alc) alc[t] = CUDART_NAN;
@@ -294,7 +383,7 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
         }
         if (fused) {
             __syncthreads();
-            if (warp == 0) {
+            if (warp == 0 && rank == 0) {
                 double m = 0.0;
                 for (int t = lane; t < nm; t += 32) m = fma(S.kx[t], S.alpha[t], m);
                 m = warp_sum(m);
@@ -306,9 +395,11 @@ alc_f64_kernel(AlcArgs a, int *__restrict__ counter, double *__restrict__ panel_
                 }
             }
         }
-        if (tid == 0) a.status[loc] = status;
+        if (tid == 0 && rank == 0) a.status[loc] = status;
         __syncthreads();
     }
+    // no CTA leaves while another may still read its exchange records
+    if constexpr (CL) cg::this_cluster().sync();
 }
 
 }  // namespace
@@ -320,17 +411,35 @@ lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a) {
     const size_t ld = (size_t)((a.nmax + 31) & ~31);
     // K^{-1} (n_max x ld, plus one spare row so masked reads stay inside), kx, b*,
     // design coordinates, reference location, chosen flags
-    size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 4 + (size_t)a.nmax * a.p * 8 +
+    size_t smem = ((size_t)a.nmax + 1) * ld * 8 + ld * 8 * 4 + 4 * ld * 8 + (size_t)a.nmax * a.p * 8 +
                   (size_t)a.p * 8 + (size_t)a.Npmax + 16;
     if (smem > ctx->smem_optin) return lagp_fail(ctx, LAGP_EINVAL, "lagp_alc_select: shared memory");
-    cudaFuncSetAttribute(alc_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f64_kernel, F64_THREADS, smem);
-    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key("alc_f64", 0, a.nmax, a.p, a.mean != nullptr), 2);
-    if (occ > 0 && per_sm > occ) per_sm = occ;
-    int64_t grid = (int64_t)ctx->num_sms * per_sm;
-    if (grid > a.M) grid = a.M;
-    if (grid < 1) grid = 1;
+    // cluster size: with few locations, the CTAs of a cluster share one
+    // location's candidates, as many as keep every cluster resident at once
+    // (at most 4; 1 = no clusters, and whenever the user fixes the CTAs per SM)
+    int cs = 1;
+    if (ctx->tuning.ctas_per_sm == 0 && ctx->tune_override == 0) {
+        cudaFuncSetAttribute(alc_f64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f64_kernel<true>, F64_THREADS, smem);
+        const int64_t fit = (int64_t)ctx->num_sms * std::max(occ, 1) / std::max<int64_t>(a.M, 1);
+        cs = (int)std::min<int64_t>(4, fit);  // (4 measured faster than 6 on the 2-d toy)
+        if (cs < 2) cs = 1;
+    }
+    int64_t grid;
+    if (cs > 1) {
+        ctx->last_alc_key = alc_shape_key("alc_f64", 0, a.nmax, a.p, a.mean != nullptr);
+        grid = a.M * cs;
+    } else {
+        cudaFuncSetAttribute(alc_f64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alc_f64_kernel<false>, F64_THREADS, smem);
+        int per_sm = alc_ctas_per_sm(ctx, alc_shape_key("alc_f64", 0, a.nmax, a.p, a.mean != nullptr), 2);
+        if (occ > 0 && per_sm > occ) per_sm = occ;
+        grid = (int64_t)ctx->num_sms * per_sm;
+        if (grid > a.M) grid = a.M;
+        if (grid < 1) grid = 1;
+    }
     char *ws = static_cast<char *>(lagp_ws(ctx, WS_ALC_PANEL,
                                            (size_t)grid * a.Npmax * ((size_t)a.nmax + 1) * 8 + 256));
     int *counter = static_cast<int *>(lagp_ws(ctx, WS_ALC_COUNTER, 256));
@@ -338,7 +447,23 @@ lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a) {
     double *panel = reinterpret_cast<double *>(ws);
     double *kappa = panel + (size_t)grid * a.Npmax * a.nmax;
     LAGP_CUDA(ctx, cudaMemsetAsync(counter, 0, sizeof(int), st));
-    alc_f64_kernel<<<(unsigned)grid, F64_THREADS, smem, st>>>(a, counter, panel, kappa);
+    if (cs > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3(F64_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        LAGP_CUDA(ctx, cudaLaunchKernelEx(&cfg, alc_f64_kernel<true>, a, counter, panel, kappa));
+    } else {
+        alc_f64_kernel<false><<<(unsigned)grid, F64_THREADS, smem, st>>>(a, counter, panel, kappa);
+    }
     ctx->launches++;
     LAGP_CUDA(ctx, cudaGetLastError());
     return LAGP_OK;

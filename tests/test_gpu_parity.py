@@ -211,6 +211,41 @@ def test_select_toy2d_full_config_f64(L, O):
     _select_case(L, O, W.c1_toy2d_fp64(), "f64", max_diverged=0.03)
 
 
+def test_select_f64_cluster_split_equals_one_cta(L, O):
+    """With few locations the plain FP64 form gives each location a cluster
+    of CTAs (candidates split across them, the argmax exchanged through
+    distributed shared memory, the same update in every CTA); its designs,
+    ALC values and fused predictions must equal the one-CTA-per-location
+    kernel's bit for bit (fixing the CTAs per SM turns the clusters off)."""
+    w = W.c1_toy2d_fp64()
+    idx = O.knn(w.X, w.Xref, 1000)
+    args = (dev(w.X), dev(w.Y), dev(w.Xref), dev(idx), 6, 50, w.d, w.g)
+    split = L.lagp_alc_predict(*args, prec="f64", want_alc=True)
+    L.set_tuning(ctas_per_sm=2)
+    try:
+        one = L.lagp_alc_predict(*args, prec="f64", want_alc=True)
+    finally:
+        L.set_tuning(ctas_per_sm=0)
+    torch.cuda.synchronize()
+    for k in ("sel", "alc", "mean", "s2", "status"):
+        assert torch.equal(torch.nan_to_num(split[k]), torch.nan_to_num(one[k])), k
+    # and a ragged batch of few locations (some with n = n0, one invalid)
+    n_arr = np.array([6, 50, 17, 33, 1, 50, 49], np.int32)
+    split = L.lagp_alc_select(dev(w.X), dev(w.Xref[:7]), dev(idx[:7]), 6, n_arr, w.d, w.g, prec="f64",
+                              n_max=50, want_alc=True)
+    L.set_tuning(ctas_per_sm=2)
+    try:
+        one = L.lagp_alc_select(dev(w.X), dev(w.Xref[:7]), dev(idx[:7]), 6, n_arr, w.d, w.g, prec="f64",
+                                n_max=50, want_alc=True)
+    finally:
+        L.set_tuning(ctas_per_sm=0)
+    torch.cuda.synchronize()
+    st = split["status"].cpu().numpy()
+    assert st[4] == 1 and (np.delete(st, 4) == 0).all()
+    for k in ("sel", "alc", "status"):
+        assert torch.equal(torch.nan_to_num(split[k]), torch.nan_to_num(one[k])), k
+
+
 def test_select_toy2d_full_config_f64schur(L, O):
     """The full 2-d configuration through the FP64 Schur (incremental O(j))
     form: its state is FP64, so it meets the near-tie rule like the plain
