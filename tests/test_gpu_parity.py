@@ -417,8 +417,16 @@ def test_mle_matches_oracle(L, O):
     sel = O.alc_select(w.X, w.Xref, idx, 6, 40, 2.0, 1e-4)["sel"]
     d0 = rng.uniform(0.5, 4.0, 24)
     ref = O.mle(w.X, w.Y, sel, 40, d0, 1e-4, 1e-3, 20.0, 10)
+    L.mle_work()  # reset the work counters
     out = L.lagp_mle_step(dev(w.X), dev(w.Y), dev(sel), 40, d0, 1e-4, 1e-3, 20.0, 10)
     np.testing.assert_allclose(out["d"].cpu().numpy(), ref["d"], rtol=1e-6)
+    assert np.array_equal(out["iters"].cpu().numpy(), ref["iters"])
+    # the kernel's FP64 work count (the bench's MLE roofline): one derivative
+    # evaluation at d0 and one per accepted step, one factorisation per
+    # evaluation of l and at least one per derivative evaluation
+    work, it, n3 = L.mle_work(), out["iters"].cpu().numpy(), 40 ** 3
+    assert 24 * n3 <= work["derivs_n3"] <= int((1 + it).sum()) * n3
+    assert work["llik_n3"] >= work["derivs_n3"] and work["llik_n3"] % n3 == 0
     np.testing.assert_allclose(out["llik"].cpu().numpy(), ref["llik"], rtol=1e-9)
     scale = np.abs(ref["llik"]) / ref["d"]
     np.testing.assert_allclose(out["dllik"].cpu().numpy(), ref["dllik"], rtol=1e-5, atol=1e-7 * scale.max())
