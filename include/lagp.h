@@ -97,7 +97,9 @@ typedef struct {
                                dropped.  (F64SCHUR: the contenders re-scored,
                                0 = 8.) */
     double rescore_rel;     /* F32BULK: cap of the contender margin (default
-                               0.5).  A candidate is a contender when its FP32
+                               0.5; a higher cap trades speed for fewer
+                               decisions missed where the FP32 state is poor).
+                               A candidate is a contender when its FP32
                                score is within the margin of the FP32 maximum;
                                the margin is 8x the largest relative
                                FP32-vs-double-float score error observed on
