@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["f32bulk", "f64", "f64schur"], default="f32bulk")
+    ap.add_argument("--prec", choices=["f32bulk", "f32bulk_f64", "f64", "f64schur"], default="f32bulk")
     ap.add_argument("--no-f64", action="store_true", help="skip the FP64-plain comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -523,6 +523,8 @@ def other_configs(L, dev, args, flush):
     for name, make, steps, warm in legs:
         w = make()
         out[name] = config_leg(L, dev, w, "f32bulk", steps, warm, flush, oracle_S=1000)
+        # the same with FP64 decisions and FP64 inverse update (smaller oracle sample)
+        out[name + "_f32bulk_f64"] = config_leg(L, dev, w, "f32bulk_f64", steps, warm, flush, oracle_S=300)
         if make is W.c5_borehole_4m:
             # end to end through the public host-buffer call: kNN, search, MLE,
             # predict, with the copies in both directions inside
@@ -718,6 +720,31 @@ def run_ours(args, rank, world, local_rank):
             f64s["identical_designs_frac_vs_f64_plain"] = float(
                 (ss["sel"] == s64["sel"]).all(dim=1).float().mean().item())
 
+    # the FP32-bulk form with FP64 decisions and FP64 inverse update (the
+    # K^{-1}-basis re-score) on the same batch
+    f32x64 = None
+    if not args.no_f64 and args.prec == "f32bulk":
+        x_ms, x_alc = [], []
+        L.lagp_autotune(X, Xr, idx0, n0, n, d, g, prec="f32bulk_f64", Y=Y)
+        for it in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            sx, px = step("f32bulk_f64", (a0, a1))
+            e1.record(stream)
+            barrier()
+            if it > 0:
+                x_ms.append(e0.elapsed_time(e1))
+                x_alc.append(a0.elapsed_time(a1))
+        ms_x = statistics.mean(x_ms)
+        f32x64 = {"value": M / (ms_x / 1e3), "unit": "predictions/s", "ms_per_step": ms_x,
+                  "alc_kernel_ms": statistics.mean(x_alc),
+                  "rmse": float(np.sqrt(np.mean((px["mean"].cpu().numpy() - w.truth) ** 2))),
+                  "identical_designs_frac_vs_f32bulk":
+                      float((sx["sel"] == s["sel"]).all(dim=1).float().mean().item())}
+
     # end to end through the public host-buffer call (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -815,6 +842,7 @@ def run_ours(args, rank, world, local_rank):
         "cuda_graph": graph_ms,
         "f64_plain": f64,
         "f64_schur": f64s,
+        "f32bulk_f64": f32x64,
         "rmse_vs_truth": rmse, "status_ok_frac": float((st == 0).mean()),
         "cand_evals_per_sec": M * world * E / alc_avg,
         "alc_kernel_ms": 1e3 * alc_avg,

@@ -80,8 +80,21 @@ typedef enum { LAGP_F64 = 0, LAGP_F32 = 1 } lagp_dtype;
  *                    state in FP64 (the incremental O(j) form of the
  *                    criterion, exact to FP64 rounding); the contenders
  *                    within a margin of 1e-5 of the best score are
- *                    re-scored with Eq. (dxy) as above. */
-typedef enum { LAGP_PREC_F64 = 0, LAGP_PREC_F32BULK = 1, LAGP_PREC_F64SCHUR = 2 } lagp_precision;
+ *                    re-scored with Eq. (dxy) as above.
+ *  LAGP_PREC_F32BULK_F64 the FP32 screen of LAGP_PREC_F32BULK with its
+ *                    contenders re-scored by Eq. (dxy) in FP64 against
+ *                    K_j^{-1}, grown by the FP64 partitioned inverse (the
+ *                    FP32-bulk form with an FP64 update); faster than
+ *                    LAGP_PREC_F32BULK where many contenders a step are
+ *                    re-scored, its decisions carrying the K^{-1} basis's
+ *                    ~cond(K_j) 2^-53 error.  Breakdowns are redone by
+ *                    LAGP_PREC_F64SCHUR like LAGP_PREC_F32BULK's. */
+typedef enum {
+    LAGP_PREC_F64 = 0,
+    LAGP_PREC_F32BULK = 1,
+    LAGP_PREC_F64SCHUR = 2,
+    LAGP_PREC_F32BULK_F64 = 3
+} lagp_precision;
 
 typedef struct lagp_ctx lagp_ctx;
 
@@ -251,7 +264,8 @@ lagp_status lagp_knn_tc_stall(lagp_ctx *ctx);
  *   n           M final design sizes (n0 <= n[m] <= Nprime[m]), or NULL
  *               (all = n_max)
  *   d           M lengthscales (> 0);  g  nugget (>= 0)
- *   prec        LAGP_PREC_F64, LAGP_PREC_F32BULK or LAGP_PREC_F64SCHUR (see lagp_precision)
+ *   prec        LAGP_PREC_F64, LAGP_PREC_F32BULK, LAGP_PREC_F64SCHUR or LAGP_PREC_F32BULK_F64
+ *               (see lagp_precision)
  *   sel         M x n_max int32 output: the chosen design rows in the order
  *               chosen (the n0 seeds first); -1 past n[m]
  *   alc         M x n_max FP64 output or NULL: raw Delta of Eq. (dxy) of the

@@ -1,8 +1,8 @@
 // a2..a6 in the Schur-complement (incremental) form with the candidate state
 // in FP64 -- the FP64 Schur form of the greedy ALC local design search
-// (Fig. 1 step 2 of the paper) -- and every decision in FP64.  (The same form
-// with the candidate state in FP32 and the decisions in double-float is
-// alc_bulk32.cu.)
+// (Fig. 1 step 2 of the paper) -- or in FP32 (the FP32-bulk form with FP64
+// decisions and FP64 inverse update), and every decision in FP64.  (The FP32
+// state with the decisions in double-float is alc_bulk32.cu.)
 //
 // Why not K_j^{-1} in FP32: the local matrices of these workloads are
 // ill-conditioned (cond(K_j) ~ 1e5..1e7 for nuggets 1e-4..1e-6), so the FP32
@@ -60,6 +60,8 @@ constexpr int F32_WARPS = F32_THREADS / 32;
 // with FP64 state the FP32 scores only round (the state is exact to FP64
 // rounding), so the margin's floor is a few FP32 ulps
 constexpr float MARGIN_MIN_F64STATE = 1e-5f;
+// with FP32 state the FP32 scores carry the recurrence's own error
+constexpr float MARGIN_MIN_F32STATE = 0.02f;
 constexpr float MARGIN_KAPPA = 8.0f;
 constexpr float ERR_DECAY = 0.75f;
 constexpr float ERR_INIT = 0.05f;
@@ -71,8 +73,10 @@ using alc::warp_best3;
 
 // K = exp(a) for the bulk state (table method)
 __device__ __forceinline__ double bulk_exp(double a, const double *etab) { return exp64_tang(a, etab); }
+__device__ __forceinline__ float bulk_exp(float a, const double *) { return __expf(a); }
 
 // FP32 screening score r^2 / v of the FP64 bulk state
+__device__ __forceinline__ float bulk_score(float cov, float v, float gf) { return cov * cov / fmaxf(v, gf); }
 __device__ __forceinline__ float bulk_score(double cov, double v, float gf) {
     const float c = (float)cov;
     return c * c / fmaxf((float)v, gf);
@@ -132,7 +136,7 @@ __device__ __forceinline__ void partial_contract(const double *kc, const double 
 // candidate coordinates): double.
 template <typename T, int CPT>
 constexpr int bulk_min_blocks() {
-    return CPT >= 8 ? 1 : 2;
+    return sizeof(T) == 8 ? (CPT >= 8 ? 1 : 2) : (CPT >= 16 ? 2 : (CPT >= 8 ? 3 : 4));
 }
 
 template <int CPT, typename T>
@@ -233,7 +237,8 @@ alc_bulk_kernel(F32Params P) {
         for (int i = tid; i < p; i += F32_THREADS) xq[i] = load_coord64(a.Xref, loc, p, i, a.dtype);
         for (int e = tid; e < p * Npad; e += F32_THREADS) {
             int i = e / Npad, c = e - i * Npad;
-            Cg[e] = c < k ? load_coord64(a.X, cands[c], p, i, a.dtype) : 0.0;
+            if constexpr (sizeof(T) == 8) Cg[e] = c < k ? load_coord64(a.X, cands[c], p, i, a.dtype) : 0.0;
+            else Cg[e] = c < k ? load_coord32(a.X, cands[c], p, i, a.dtype) : 0.f;
         }
         const double inv_d64 = 1.0 / d, onepg = 1.0 + g;
         if (tid == 0) {
@@ -246,7 +251,7 @@ alc_bulk_kernel(F32Params P) {
         __syncthreads();
         const T inv_d = (T)(1.0 / d);
         const float gf = fmaxf((float)g, FLT_MIN);  // floor of v in the FP32 scores
-        const T gT = (T)fmax(g, DBL_MIN);
+        const T gT = sizeof(T) == 8 ? (T)fmax(g, DBL_MIN) : (T)fmaxf((float)g, FLT_MIN);
         T v[CPT], cov[CPT];
         float score[CPT];
         int rows[CPT];  // design rows of this thread's candidates (tie-break key)
@@ -300,7 +305,8 @@ alc_bulk_kernel(F32Params P) {
                 }
             } else {
                 const float margin =
-                    fminf(P.rel, fmaxf(MARGIN_MIN_F64STATE, MARGIN_KAPPA * s_err));
+                    fminf(P.rel, fmaxf(sizeof(T) == 8 ? MARGIN_MIN_F64STATE : MARGIN_MIN_F32STATE,
+                                       MARGIN_KAPPA * s_err));
                 float gmax = w_max[0];
 #pragma unroll
                 for (int w = 1; w < F32_WARPS; w++) gmax = fmaxf(gmax, w_max[w]);
@@ -592,7 +598,9 @@ alc_bulk_kernel(F32Params P) {
             for (int r = 0; r < CPT; r++)
                 if (c0 + r == cstar) {
                     const T vs = v[r] > gT ? v[r] : gT;
-                    const T il = 1.0 / sqrt(vs);
+                    T il;
+                    if constexpr (sizeof(T) == 8) il = 1.0 / sqrt(vs);
+                    else il = rsqrtf(vs);
                     s_invlam = il;
                     s_wnew = cov[r] * il;
                     chosen |= 1u << r;
@@ -608,7 +616,7 @@ alc_bulk_kernel(F32Params P) {
                 for (int r = 0; r < CPT; r++) acc[r] = T(0);
                 const T *Ub = U + c0;
                 // loads in flight per thread: UNR rows of CPT values
-                constexpr int UNR = 2;
+                constexpr int UNR = (sizeof(T) == 8 || CPT >= 16) ? 2 : 6;
                 int i = 0;
                 for (; i + UNR <= j; i += UNR) {
                     T u[UNR][CPT];
@@ -679,7 +687,10 @@ alc_bulk_kernel(F32Params P) {
                 a.df[loc] = ok ? (double)nm : CUDART_NAN;
             }
         }
-        if (tid == 0) a.status[loc] = status;
+        if (tid == 0) {
+            a.status[loc] = status;
+            if (status == LAGP_ENOTPD && a.fail_count) atomicAdd(a.fail_count, 1);  // (the FP64 Schur retry)
+        }
         __syncthreads();
     }
     if (tid < 4 && P.work) atomicAdd(P.work + tid, s_work[tid]);
@@ -712,7 +723,7 @@ lagp_status launch_cpt(lagp_ctx *ctx, const AlcArgs &a) {
     const size_t smem = etab_smem ? smem_tab : smem_notab;
     if (!etab_smem) occ = occ_notab;
     const bool f64state = sizeof(T) == 8;
-    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key(f64state ? "alc_f64schur" : "alc_f32", CPT, a.nmax, a.p,
+    int per_sm = alc_ctas_per_sm(ctx, alc_shape_key(f64state ? "alc_f64schur" : "alc_f32x64", CPT, a.nmax, a.p,
                                                     a.mean != nullptr),
                                  f64state ? 2 : 4);
     if (occ > 0 && per_sm > occ) per_sm = occ;
@@ -749,3 +760,4 @@ lagp_status launch_bulk(lagp_ctx *ctx, const AlcArgs &a) {
 }  // namespace
 
 lagp_status launch_alc_f64schur(lagp_ctx *ctx, const AlcArgs &a) { return launch_bulk<double>(ctx, a); }
+lagp_status launch_alc_f32x64(lagp_ctx *ctx, const AlcArgs &a) { return launch_bulk<float>(ctx, a); }

@@ -53,7 +53,7 @@ extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, in
     cudaEvent_t e0, e1;
     LAGP_CUDA(ctx, cudaEventCreate(&e0));
     LAGP_CUDA(ctx, cudaEventCreate(&e1));
-    const int max_cps = prec == LAGP_PREC_F32BULK ? 4 : 3;
+    const int max_cps = (prec == LAGP_PREC_F32BULK || prec == LAGP_PREC_F32BULK_F64) ? 4 : 3;
     // the FP32-bulk kernel's re-score batch too (unless the user fixed it)
     const bool tune_b = prec == LAGP_PREC_F32BULK && ctx->tuning.rescore_max == 0;
     const int batches[2] = {8, 4};

@@ -253,24 +253,25 @@ static lagp_status alc_common(lagp_ctx *ctx, const char *fn, const void *X, int6
     if (n0 < 1 || n_max < n0 || n_max > Nprime_max || n_max > 128)
         return lagp_fail(ctx, LAGP_EINVAL, f + ": need 1 <= n0 <= n_max <= min(Nprime_max, 128)");
     if (!(g >= 0.0) || !std::isfinite(g)) return lagp_fail(ctx, LAGP_EINVAL, f + ": g must be >= 0");
-    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK && prec != LAGP_PREC_F64SCHUR)
+    if (prec != LAGP_PREC_F64 && prec != LAGP_PREC_F32BULK && prec != LAGP_PREC_F64SCHUR &&
+        prec != LAGP_PREC_F32BULK_F64)
         return lagp_fail(ctx, LAGP_EINVAL, f + ": unknown precision");
     LAGP_CUDA(ctx, cudaSetDevice(ctx->device));
     AlcArgs a{X, N, p, dtype, Xref, M, idx, Nprime, Nprime_max, n0, n, n_max, d, g, sel, alc, status,
               Y, mean, s2, df};
     if (prec == LAGP_PREC_F64) return launch_alc_f64(ctx, a);
     if (prec == LAGP_PREC_F64SCHUR) return launch_alc_f64schur(ctx, a);
-    // FP32-bulk: the locations where the FP32 screen broke down (the
-    // double-float check found no contender with m^{-1} > 0: near-singular
-    // local matrices) are redone by the FP64 Schur form in a second launch
-    // that returns at once when there are none
+    // FP32-bulk (either re-score): the locations where the FP32 screen broke
+    // down (no contender with m^{-1} > 0: near-singular local matrices) are
+    // redone by the FP64 Schur form in a second launch that returns at once
+    // when there are none
     int *cnt = nullptr;
     unsigned long long *wk = nullptr;
     LAGP_TRY(alc_counters(ctx, &cnt, &wk));
     int *fails = reinterpret_cast<int *>(reinterpret_cast<char *>(cnt) + 64);
     LAGP_CUDA(ctx, cudaMemsetAsync(fails, 0, sizeof(int), ctx->stream));
     a.fail_count = fails;
-    LAGP_TRY(launch_alc_f32(ctx, a));
+    LAGP_TRY(prec == LAGP_PREC_F32BULK ? launch_alc_f32(ctx, a) : launch_alc_f32x64(ctx, a));
     const std::string key = ctx->last_alc_key;  // (the autotuner records under the FP32-bulk key)
     AlcArgs r = a;
     r.fail_count = nullptr;

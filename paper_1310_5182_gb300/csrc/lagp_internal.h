@@ -128,6 +128,7 @@ struct AlcArgs {
 lagp_status launch_alc_f64(lagp_ctx *ctx, const AlcArgs &a);
 lagp_status launch_alc_f32(lagp_ctx *ctx, const AlcArgs &a);
 lagp_status launch_alc_f64schur(lagp_ctx *ctx, const AlcArgs &a);
+lagp_status launch_alc_f32x64(lagp_ctx *ctx, const AlcArgs &a);
 
 struct GpArgs {
     const void *X;

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "liblagp.so")
 
 LAGP_OK, LAGP_EINVAL, LAGP_ENOTPD, LAGP_ECUDA, LAGP_ETIMEOUT, LAGP_ENOMEM = range(6)
 LAGP_F64, LAGP_F32 = 0, 1
-LAGP_PREC_F64, LAGP_PREC_F32BULK, LAGP_PREC_F64SCHUR = 0, 1, 2
-_PREC = {"f64": LAGP_PREC_F64, "f32bulk": LAGP_PREC_F32BULK, "f64schur": LAGP_PREC_F64SCHUR}
+LAGP_PREC_F64, LAGP_PREC_F32BULK, LAGP_PREC_F64SCHUR, LAGP_PREC_F32BULK_F64 = 0, 1, 2, 3
+_PREC = {"f64": LAGP_PREC_F64, "f32bulk": LAGP_PREC_F32BULK, "f64schur": LAGP_PREC_F64SCHUR,
+         "f32bulk_f64": LAGP_PREC_F32BULK_F64}
 
 
 class LagpError(RuntimeError):

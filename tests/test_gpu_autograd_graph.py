@@ -66,7 +66,7 @@ def test_local_loglik_gradients(L):
     np.testing.assert_allclose(d.grad.cpu().numpy(), ref["dllik"], rtol=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("prec", ["f32bulk", "f64", "f64schur"])
+@pytest.mark.parametrize("prec", ["f32bulk", "f32bulk_f64", "f64", "f64schur"])
 def test_search_captured_in_cuda_graph(L, prec):
     """kNN and the fused search+prediction, captured once and replayed: the
     persistent kernels and their work counters (reset by captured memsets)

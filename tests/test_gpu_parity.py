@@ -267,7 +267,22 @@ def test_select_toy2d_full_config_f32bulk(L, O):
     assert abs(r32 - r64) <= 0.02 * r64
 
 
-@pytest.mark.parametrize("prec", ["f32bulk", "f64schur"])
+def test_select_toy2d_full_config_f32bulk_f64_bound(L, O):
+    """The 2-d configuration through the FP32-bulk form with the FP64 re-score
+    in the K^{-1} basis: its Delta ~ 1e-7 late in the search sits at the FP32
+    screen's resolution and its re-score carries cond(K_j) 2^-53, so its
+    stated bound is: at most 5% of locations leave the oracle's trajectory,
+    each at a step whose oracle gap is below 1%; RMSE within 2%."""
+    w = W.c1_toy2d_fp64()
+    _select_case(L, O, w, "f32bulk_f64", max_diverged=0.05, gap_rel=1e-2)
+    out = L.lagp_agp(w.X, w.Y, w.Xref, 6, 50, 1000, w.d, w.g, prec="f32bulk_f64")
+    ref = O.run_pipeline(w.X, w.Y, w.Xref, 6, 50, 1000, w.d, w.g)
+    r32 = np.sqrt(np.mean((out["mean"] - w.truth) ** 2))
+    r64 = np.sqrt(np.mean((ref["mean"] - w.truth) ** 2))
+    assert abs(r32 - r64) <= 0.02 * r64
+
+
+@pytest.mark.parametrize("prec", ["f32bulk", "f32bulk_f64", "f64schur"])
 def test_search_ill_conditioned_clustered(L, O, prec):
     """An ill-conditioned case: a design of tight clusters (1,000 clusters of
     half-width 0.02, d = 0.05) with nugget g = 1e-7, local matrices with
@@ -306,7 +321,7 @@ def test_search_ill_conditioned_clustered(L, O, prec):
     print(f"{prec}: fused prediction's largest relative drift {drift.max():.2e}")
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f32bulk_f64", "f64schur"])
 def test_select_ragged_uneven(L, O, prec):
     """Uneven n and N' per location (several tiles of candidates, ragged tails)."""
     rng = np.random.default_rng(23)
@@ -317,13 +332,13 @@ def test_select_ragged_uneven(L, O, prec):
     _select_case(L, O, w, prec, Np_arr=Np_arr, n_arr=n_arr, max_diverged=0.05)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f32bulk_f64", "f64schur"])
 def test_select_slab3d(L, O, prec):
     w = W.slab3d(seed=8, N=30_000, grid=(4, 4, 3), n=30, Np=300)
     _select_case(L, O, w, prec, max_diverged=0.05)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f32bulk_f64", "f64schur"])
 def test_select_edge_cases(L, O, prec):
     rng = np.random.default_rng(24)
     w = W.toy2d(seed=9, N=500, M=6, Np=40, n=6)
@@ -358,7 +373,7 @@ def test_select_deterministic(L, O):
 
 # -------------------------------------------- search + fused prediction (a2..a7)
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f32bulk_f64", "f64schur"])
 def test_alc_predict_fused_matches_oracle(L, O, prec):
     """The fused entry point: its designs meet the selection rule and its
     predictions (grown by the partitioned inverse) match the oracle's
@@ -504,7 +519,7 @@ def test_agp_host_buffers_match_oracle(L, O):
                ref["d"], w.g)
 
 
-@pytest.mark.parametrize("prec", ["f32bulk", "f64", "f64schur"])
+@pytest.mark.parametrize("prec", ["f32bulk", "f32bulk_f64", "f64", "f64schur"])
 def test_agp_two_stage(L, O, prec):
     """Fig. 1 step 4 with two rounds: search at d0, MLE, search again at the
     local estimates, MLE from them, predict.  Each stage is checked against
@@ -538,7 +553,7 @@ def test_agp_two_stage(L, O, prec):
     np.testing.assert_array_equal(out["s2"], pr["s2"].cpu().numpy())
 
 
-@pytest.mark.parametrize("prec", ["f32bulk", "f64", "f64schur"])
+@pytest.mark.parametrize("prec", ["f32bulk", "f32bulk_f64", "f64", "f64schur"])
 def test_borehole_full_size_sampled(L, O, prec):
     """The full 8-d borehole configuration (N=100,000, M=10,000, (6, 50, 1000),
     d=2, g=1e-6) run whole on the GPU, exactly as the benchmark launches it;
@@ -680,7 +695,7 @@ def test_alc_eval_matches_oracle(L, O, n):
 
 # -------------------------------------- separable lengthscales (Sec. 3.1)
 
-@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f64schur"])
+@pytest.mark.parametrize("prec", ["f64", "f32bulk", "f32bulk_f64", "f64schur"])
 def test_separable_search_and_predict_match_oracle(L, O, prec):
     """Inputs scaled by lagp_scale_inputs, searched and predicted with d = 1,
     against the oracle's separable correlation written from its definition
