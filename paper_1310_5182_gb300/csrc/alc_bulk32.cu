@@ -84,8 +84,9 @@ constexpr int DTHREADS = THREADS - FTHREADS;  // double-float group: warps 4..7
 constexpr int DWARPS = DTHREADS / 32;
 // Adaptive contender margin: FP32 scores within `margin` (relative) of the
 // FP32 maximum are re-scored, margin = min(rescore_rel, max(MARGIN_MIN,
-// MARGIN_KAPPA * err)), err = the largest relative FP32-vs-double-float score
-// error seen among the contenders re-scored so far, decaying by ERR_DECAY
+// MARGIN_KAPPA * err)), err = the largest FP32-vs-double-float score error
+// seen among the contenders re-scored so far, relative to the step's best
+// score (what decides whether the best can be missed), decaying by ERR_DECAY
 // per step (from ERR_INIT, which puts the first margin at its floor: after
 // n0 steps of the recurrence the FP32 state is still close to exact, and the
 // first re-scores measure its error).
@@ -711,8 +712,9 @@ alc_bulk32_kernel(B32Params P) {
                                 bv = bat_v[lane];
                                 bc = bat_r[lane];
                             }
-                            if (j >= a.n0 && dl.hi > 0.f)
-                                err = fabsf(__fdividef(bat_s[lane], dl.hi) - 1.f);
+                            // (the error against the step's best score below:
+                            // a low contender's error cannot displace the best)
+                            if (j >= a.n0 && dl.hi > 0.f) err = fabsf(bat_s[lane] - dl.hi);
                         }
                     }
                     int wl = lane;
@@ -737,8 +739,8 @@ alc_bulk32_kernel(B32Params P) {
                         err = fmaxf(err, __shfl_xor_sync(LAGP_FULL_MASK, err, o));
                     }
                     if (lane == 0) {
-                        s_steperr = fmaxf(s_steperr, err);
                         const dfl bd = ld2(&best_dl);
+                        s_steperr = fmaxf(s_steperr, err);  // (absolute: divided by the step's best below)
                         const bool improved = slot >= 0 && (df_gt(dl, bd) || (!df_gt(bd, dl) && row < best_row));
                         if (improved) {
                             st2(&best_dl, dl);
@@ -794,7 +796,9 @@ alc_bulk32_kernel(B32Params P) {
                 // the ALC value (a lone contender's Delta is computed here) and
                 // the contender margin's error estimate
                 dfl dl = ld2(&best_dl);
-                float err = s_steperr;
+                // the batches' largest error over the step's best score (the
+                // same whatever the batches)
+                float err = dl.hi > 0.f ? __fdividef(s_steperr, dl.hi) : 0.f;
                 if (lone) {
                     dl = df_div(df_sqr(ld2(con_r)), ld2(con_v));
                     if (j >= a.n0 && dl.hi > 0.f) err = fabsf(__fdividef(bat_s[0], dl.hi) - 1.f);

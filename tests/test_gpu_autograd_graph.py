@@ -148,10 +148,12 @@ def test_autotune_picks_a_grid_and_results_do_not_depend_on_it(L):
     after = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
     for k in ("sel", "mean", "s2", "alc"):
         assert torch.equal(torch.nan_to_num(before[k]), torch.nan_to_num(after[k])), k
-    for cps in (1, 3):
-        for b in (1, 3, 8):
-            L.set_tuning(ctas_per_sm=cps, rescore_max=b)
-            out = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
-            for k in ("sel", "mean", "s2", "alc"):
-                assert torch.equal(torch.nan_to_num(before[k]), torch.nan_to_num(out[k])), (cps, b, k)
-    L.set_tuning(ctas_per_sm=0, rescore_max=0)
+    try:
+        for cps in (1, 3):
+            for b in (1, 3, 8):
+                L.set_tuning(ctas_per_sm=cps, rescore_max=b)
+                out = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
+                for k in ("sel", "mean", "s2", "alc"):
+                    assert torch.equal(torch.nan_to_num(before[k]), torch.nan_to_num(out[k])), (cps, b, k)
+    finally:
+        L.set_tuning(ctas_per_sm=0, rescore_max=0)
