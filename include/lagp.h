@@ -107,8 +107,10 @@ typedef struct {
                                batch, 1..32, used up to 8; 0 = automatic (the
                                autotuner's choice for the shape, else 8).
                                More contenders take further batches, none is
-                               dropped.  (F64SCHUR: the contenders re-scored,
-                               0 = 8.) */
+                               dropped.  (F64SCHUR and F32BULK_F64: the
+                               contenders re-scored, 0 = 8; beyond it those
+                               with the lowest FP32 scores are not re-scored,
+                               a bound on the work those forms accept.) */
     double rescore_rel;     /* F32BULK: cap of the contender margin (default
                                0.5; a higher cap trades speed for fewer
                                decisions missed where the FP32 state is poor).
