@@ -20,7 +20,8 @@
 //               expansion_margin, screen_margin) and counting the rows below
 //               tau0.  A query whose count is short of N', or whose buffer
 //               overflowed, is redone by a second launch with stride 1 (the
-//               exact method).
+//               exact method), where a block with at most four such queries
+//               gives each a team of warps that share its sweep.
 //   knn_sort    one CTA per query: exact FP64 distances of the collected rows
 //               (separately rounded subtract/multiply/add in coordinate order,
 //               on the original coordinates), bitonic sort on (d2, row), first
@@ -276,14 +277,15 @@ __device__ void find_bin(const uint32_t *h, uint32_t target, int lane, uint32_t 
     }
 }
 
-// One design tile against a warp's QPW queries.  PASS 0: level-1 histogram;
-// PASS 1: level-2 histogram inside the boundary bin; PASS 2: collection.
+// One design tile against a warp's QPW queries, rows r0, r0 + rstep, ... of
+// the tile.  PASS 0: level-1 histogram; PASS 1: level-2 histogram inside the
+// boundary bin; PASS 2: collection.
 // Tile row pt holds (y_0 .. y_{p-1}, |y|^2) of a centred design row, with
 // row stride PS.  EXP: s = max(0, |y_x|^2 + |y_q|^2 - 2 y_x . y_q) with
 // qr = -2 y_q and qn = |y_q|^2 (negative values, from rounding, clamped to 0);
 // otherwise s = sum (y_x - y_q)^2 with qr = y_q.
 template <int P, int PASS, bool EXP>
-__device__ __forceinline__ void screen_tile(const float *t, int ps_rt, int cnt, int lane, int p,
+__device__ __forceinline__ void screen_tile(const float *t, int ps_rt, int cnt, int r0, int rstep, int p,
                                             const float (&qr)[QPW][P > 0 ? P : 1],
                                             const float (&qn)[QPW], const float *qsw,
                                             const bool (&ok)[QPW], uint32_t *histw,
@@ -293,7 +295,7 @@ __device__ __forceinline__ void screen_tile(const float *t, int ps_rt, int cnt, 
                                             int32_t Cmax, int64_t base) {
     const int np = P > 0 ? P : p;
     const int PS = P > 0 ? ((P + 1) | 1) : ps_rt;
-    for (int pt = lane; pt < cnt; pt += 32) {
+    for (int pt = r0; pt < cnt; pt += rstep) {
         const float *row = t + pt * PS;
         float sd[QPW];
         if constexpr (EXP) {
@@ -377,12 +379,16 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
     const int TT = tile_len(pp);               // rows per tile
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem_raw);   // QB x HB
     float *tiles = reinterpret_cast<float *>(hist + QB * HB);  // 2 x TT x pp, 16-byte aligned
-    float *qs = tiles + 2 * (size_t)TT * pp;                     // QB x pp: centred queries
-    __shared__ int32_t s_count[QB], s_count0[QB];
+    float *qs = tiles + 2 * (size_t)TT * pp;                     // (QB + 1) x pp: centred queries
+    __shared__ int32_t s_count[QB], s_count0[QB], s_flag[QB], s_rt[QB];
     __shared__ int64_t s_blk;
     __shared__ double s_c[64], s_B;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) centre_and_bound(kmax, kmin, p, s_c, s_B);
+    // a spare zero slot past the QB queries (read, never used, by the second
+    // query slot of a warp that screens the last query of a block together
+    // with other warps)
+    for (int i = threadIdx.x; i < pp; i += SCREEN_THREADS) qs[QB * pp + i] = 0.f;
     __syncthreads();
     const double B = s_B;
     const int64_t nsamp = (N + stride - 1) / stride;
@@ -420,19 +426,68 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
                 for (int i = p + 1; i < pp; i++) qs[ql * pp + i] = 0.f;
             }
             for (int b = lane; b < HB; b += 32) hist[ql * HB + b] = 0;
-            if (lane == 0) s_count[ql] = s_count0[ql] = 0;
+            if (lane == 0) {
+                s_count[ql] = s_count0[ql] = 0;
+                s_flag[ql] = ok[h] ? 1 : 0;
+                s_rt[ql] = rtarget[h];
+            }
         }
         // a block without a query to screen skips the passes (not the results)
         const bool any_ok = __syncthreads_or(mine_any);
+        // The queries a warp screens: its own QPW (slots sbase, sbase + 1) or,
+        // in the exact retry of a block with at most four flagged queries,
+        // one flagged query shared by a team of W = 8 / nf warps (nf rounded
+        // up to a power of two; a team of four idle when nf = 3).  A team
+        // splits every tile's rows (warp `sub` of the team takes the 32-row
+        // groups sub, sub + W, ...) and adds into the query's one histogram
+        // and counters, so that one query's sweep over all N rows runs on
+        // the whole CTA instead of one warp.  The results are the same
+        // either way: the counts do not depend on which warp adds them, and
+        // the sort orders the collected rows.
+        int nf = 0;
+        if (retry_pass)
+            for (int c = 0; c < QB; c++) nf += s_flag[c];
+        const bool coop = nf >= 1 && nf <= 4;
+        int sbase = w * QPW, r0 = lane, rstep = 32;
+        bool leader = true;  // the warp that clears the team's histogram
+        bool sok[QPW];
+        int srt[QPW];
+        int64_t sq[QPW];
+#pragma unroll
+        for (int h = 0; h < QPW; h++) {
+            sok[h] = ok[h];
+            srt[h] = rtarget[h];
+            sq[h] = q[h];
+        }
+        if (coop) {
+            const int W = nf == 1 ? 8 : (nf == 2 ? 4 : 2);
+            const int team = w / W, sub = w - team * W;
+            int slot = -1;  // the team-th flagged slot
+            for (int c = 0, f = 0; c < QB; c++)
+                if (s_flag[c]) {
+                    if (f == team) slot = c;
+                    f++;
+                }
+            sbase = slot >= 0 ? slot : 0;
+#pragma unroll
+            for (int h = 0; h < QPW; h++) {
+                sok[h] = h == 0 && slot >= 0;
+                srt[h] = s_rt[sbase];
+                sq[h] = blk * QB + sbase;
+            }
+            r0 = lane + 32 * sub;
+            rstep = 32 * W;
+            leader = sub == 0;
+        }
         float qr[QPW][P > 0 ? P : 1] = {};
         float qn[QPW] = {};
 #pragma unroll
         for (int h = 0; h < QPW; h++) {
-            qn[h] = qs[(w * QPW + h) * pp + p];
+            qn[h] = qs[(sbase + h) * pp + p];
             if constexpr (P > 0) {
 #pragma unroll
                 for (int i = 0; i < P; i++) {
-                    const float y = qs[(w * QPW + h) * pp + i];
+                    const float y = qs[(sbase + h) * pp + i];
                     qr[h][i] = EXP ? -2.f * y : y;
                 }
             }
@@ -472,37 +527,44 @@ knn_screen(const float *__restrict__ Y32, const float *__restrict__ Ys, int64_t 
                 const int64_t base = tile * TT;
                 const int cnt = (int)min((int64_t)TT, nrows - base);
                 const float *t = tiles + (size_t)buf * TT * pp;
-                const float *qsw = qs + w * QPW * pp;
-                uint32_t *histw = hist + w * QPW * HB;
+                const float *qsw = qs + sbase * pp;
+                uint32_t *histw = hist + sbase * HB;
                 if (pass == 0)
-                    screen_tile<P, 0, EXP>(t, pp, cnt, lane, p, qr, qn, qsw, ok, histw, b1, tau0, tau2f,
-                                           s_count + w * QPW, s_count0 + w * QPW, cand, q, Cmax, base);
+                    screen_tile<P, 0, EXP>(t, pp, cnt, r0, rstep, p, qr, qn, qsw, sok, histw, b1, tau0, tau2f,
+                                           s_count + sbase, s_count0 + sbase, cand, sq, Cmax, base);
                 else if (pass == 1)
-                    screen_tile<P, 1, EXP>(t, pp, cnt, lane, p, qr, qn, qsw, ok, histw, b1, tau0, tau2f,
-                                           s_count + w * QPW, s_count0 + w * QPW, cand, q, Cmax, base);
+                    screen_tile<P, 1, EXP>(t, pp, cnt, r0, rstep, p, qr, qn, qsw, sok, histw, b1, tau0, tau2f,
+                                           s_count + sbase, s_count0 + sbase, cand, sq, Cmax, base);
                 else
-                    screen_tile<P, 2, EXP>(t, pp, cnt, lane, p, qr, qn, qsw, ok, histw, b1, tau0, tau2f,
-                                           s_count + w * QPW, s_count0 + w * QPW, cand, q, Cmax, base);
+                    screen_tile<P, 2, EXP>(t, pp, cnt, r0, rstep, p, qr, qn, qsw, sok, histw, b1, tau0, tau2f,
+                                           s_count + sbase, s_count0 + sbase, cand, sq, Cmax, base);
                 // the next tile has landed and every warp is done with this one
                 cp_async_wait_all();
                 __syncthreads();
             }
 #pragma unroll
             for (int h = 0; h < QPW; h++) {
-                if (!ok[h]) continue;
-                uint32_t *hh = hist + (w * QPW + h) * HB;
+                if (!sok[h]) continue;
+                const uint32_t *hh = hist + (sbase + h) * HB;
                 if (pass == 0) {
-                    find_bin(hh, (uint32_t)rtarget[h], lane, b1[h], before[h]);
-                    __syncwarp();
-                    for (int b = lane; b < HB; b += 32) hh[b] = 0;
+                    find_bin(hh, (uint32_t)srt[h], lane, b1[h], before[h]);
                 } else if (pass == 1) {
                     uint32_t b2, before2;
-                    find_bin(hh, (uint32_t)rtarget[h] - before[h], lane, b2, before2);
+                    find_bin(hh, (uint32_t)srt[h] - before[h], lane, b2, before2);
                     tau0[h] = __uint_as_float((b1[h] << L1_SHIFT) | (b2 << L2_SHIFT) | L2_LOW);
                     tau2f[h] = __double2float_rd(EXP ? expansion_margin(tau0[h], p, B)
                                                      : screen_margin(tau0[h], p, B));
                 }
-                __syncwarp();
+            }
+            if (pass == 0) {
+                // every warp of a team has read the level-1 histogram before
+                // its leader clears it for level 2
+                __syncthreads();
+                if (leader)
+#pragma unroll
+                    for (int h = 0; h < QPW; h++)
+                        if (sok[h])
+                            for (int b = lane; b < HB; b += 32) hist[(sbase + h) * HB + b] = 0;
             }
             __syncthreads();
         }
@@ -988,7 +1050,7 @@ lagp_status launch_knn(lagp_ctx *ctx, const void *X, int64_t N, int p, lagp_dtyp
     }
     int *tc_err = reinterpret_cast<int *>(meta);
 
-    size_t smem = (size_t)QB * HB * 4 + 2 * (size_t)tile_len(pp) * pp * 4 + (size_t)QB * pp * 4;
+    size_t smem = (size_t)QB * HB * 4 + 2 * (size_t)tile_len(pp) * pp * 4 + (size_t)(QB + 1) * pp * 4;
     // persistent grid: two CTAs per SM, blocks of QB queries from a counter
     const int64_t nblk = (M + QB - 1) / QB;
     dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)ctx->num_sms * 2));

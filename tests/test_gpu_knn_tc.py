@@ -140,6 +140,33 @@ def test_bounded_wait_reports_and_retries(L):
     assert L.knn_stats()["tc_failed"] == 0
 
 
+@pytest.mark.parametrize("M", [1, 3, 18, 21])
+def test_retry_teams_match_oracle(L, M):
+    """The exact retry of a block with at most four flagged queries runs each
+    one's sweep on a team of warps (8, 4 or 2 of them, the rows of every tile
+    split between them) instead of one warp.  The stall hook flags every
+    query, so that M = 1 and 3 give one block of one and three flagged
+    queries, M = 18 and 21 a full block (one warp per two queries) and one of
+    two and five (teams of four; one warp each).  Ragged N' and a duplicated
+    design row put ties at the thresholds.  The neighbour sets equal the
+    oracle's bit for bit."""
+    from oracle import oracle as orc
+    orc.build()
+    rng = np.random.default_rng(47)
+    X = rng.uniform(0, 1, (6_000, 8))
+    X[4_000:4_010] = X[17]  # equal distances at every query
+    Xr = rng.uniform(0, 1, (M, 8))
+    Np = rng.integers(150, 301, M).astype(np.int32)
+    L.knn_tc_stall()
+    idx, st = L.lagp_knn(dev(X), dev(Xr), 300, Nprime=Np)
+    stats = L.knn_stats()
+    assert stats["tc_failed"] == 1
+    assert stats["retried"] == M
+    assert (st.cpu().numpy() == 0).all()
+    ref = orc.knn(X, Xr, 300, Np=Np)
+    assert np.array_equal(idx.cpu().numpy(), ref)
+
+
 def test_non_finite_rows_both_paths(L):
     """Design rows with NaN or infinite coordinates never enter a candidate
     set on either path; the two paths agree bit for bit (statuses too)."""
