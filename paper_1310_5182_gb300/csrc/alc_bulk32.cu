@@ -60,6 +60,16 @@
 // both its row and its column reads are free of bank conflicts, zero below
 // the diagonal), w, z, the design coordinates, the contenders' vectors and
 // the FP32 v, r of every candidate.
+//
+// Code size.  A step runs from the instruction cache, and the kernel's
+// machine code (110 KB at CPT = 8 with the compiler's own unrolling) did not
+// fit: the set-up of a location and the double-float group's per-step phases
+// evicted one another.  The loops of the per-location set-up and outputs, of
+// the triangular products, of R3 and of the winner's bookkeeping therefore
+// carry `#pragma unroll 1` (85 KB); the Schur pass, the listing, R1, R2 and
+// the argmax of several contenders keep their unrolling, which the steps
+// with many contenders need.  Measured on the borehole batch: 11.4 -> 9.6 ms
+// a search, the same designs bit for bit.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -155,10 +165,12 @@ __device__ __forceinline__ dfl df_rsqrt(dfl v) {
 // time keeps the code small (it runs from the instruction cache every step).
 __device__ __noinline__ void df_tri_lower(const float2 *kc, const float2 *LT, int ldl, int s0, int s1, int j,
                                           int lane, float2 *out) {
+    #pragma unroll 1
     for (int t = lane; t < ((j + 31) & ~31); t += 32) {
         if (t < j) {
             dfl acc = df_zero();
             const float2 *row = LT + s0 * ldl + t;
+            #pragma unroll 1
             for (int s = s0; s < s1; s++, row += ldl) df_fma_acc(acc, ld2(row), ld2(kc + s));
             st2(out + t, acc);
         }
@@ -170,10 +182,12 @@ __device__ __noinline__ void df_tri_lower(const float2 *kc, const float2 *LT, in
 // stand in for the test t >= s); partials of s < t1 written to out
 __device__ __noinline__ void df_tri_upper(const float2 *us, const float2 *LT, int ldl, int t0, int t1, int lane,
                                           float2 *out) {
+    #pragma unroll 1
     for (int sb = lane; sb < ((t1 + 31) & ~31); sb += 32) {
         if (sb < t1) {
             dfl acc = df_zero();
             const float2 *col = LT + sb * ldl;
+            #pragma unroll 1
             for (int t = t0; t < t1; t++) df_fma_acc(acc, ld2(col + t), ld2(us + t));
             st2(out + sb, acc);
         }
@@ -273,9 +287,11 @@ alc_bulk32_kernel(B32Params P) {
     const int dt = tid - FTHREADS, dw = warp - FWARPS;  // index within the double-float group
     const int c0 = tid * CPT;                           // FP32 group: first candidate slot
     const bool x64 = a.dtype == LAGP_F64;
+    #pragma unroll 1
     for (int k = tid; k < EXP64_TABLE_SIZE; k += THREADS) st2(etab + k, df_from_double(exp64_table_g[k]));
     if (tid < 4) s_work[tid] = 0ull;
 
+    #pragma unroll 1
     for (;;) {
         if (tid == 0) s_loc = atomicAdd(P.counter, 1);
         __syncthreads();
@@ -294,11 +310,13 @@ alc_bulk32_kernel(B32Params P) {
                                !isfinite(d)) ? LAGP_EINVAL : LAGP_OK;
         __syncthreads();
         if (s_bad == LAGP_OK)
+            #pragma unroll 1
             for (int c = tid; c < k; c += THREADS) {
                 int32_t r = cands[c];
                 if (r < 0 || r >= a.N) s_bad = LAGP_EINVAL;
             }
         __syncthreads();
+        #pragma unroll 1
         for (int t = tid; t < nmax; t += THREADS) {
             sel[t] = -1;
             if (alc) alc[t] = CUDART_NAN;
@@ -316,8 +334,11 @@ alc_bulk32_kernel(B32Params P) {
         // diagonal spare the triangular products any per-element test), the
         // coordinates (FP32 and, for FP64 inputs, their low parts), the
         // responses, the initial FP32 state
+        #pragma unroll 1
         for (int e = tid; e < nmax * ldl; e += THREADS) LT[e] = make_float2(0.f, 0.f);
+        #pragma unroll 1
         for (int i = tid; i < p; i += THREADS) st2(xqd + i, load_df(a.Xref, loc * p + i, a.dtype));
+        #pragma unroll 1
         for (int e = tid; e < p * NPAD; e += THREADS) {
             const int i = e / NPAD, c = e - i * NPAD;
             dfl xv = df_zero();
@@ -326,6 +347,7 @@ alc_bulk32_kernel(B32Params P) {
             if (x64) Clo[e] = xv.lo;
         }
         if (fused)
+            #pragma unroll 1
             for (int c = tid; c < k; c += THREADS) st2(Yc + c, load_df(a.Y, cands[c], a.dtype));
         const dfl onepg = df_from_double(1.0 + g);
         const dfl inv_d = df_from_double(1.0 / d);
@@ -346,6 +368,7 @@ alc_bulk32_kernel(B32Params P) {
                 float s[CH];
 #pragma unroll
                 for (int r = 0; r < CH; r++) s[r] = 0.f;
+                #pragma unroll 1
                 for (int i = 0; i < p; i++) {
                     float cv[CH];
                     load_vec<CH>(Cg + i * NPAD + c0 + h, cv);
@@ -565,6 +588,7 @@ alc_bulk32_kernel(B32Params P) {
                     bat_r[dt] = e < LCAP ? lst_r[e] : ov_r[e];
                     if (fused) con_y[dt] = Yc[slot];
                 }
+                #pragma unroll 1
                 for (int e2 = dt; e2 < ncon * p; e2 += DTHREADS) {
                     const int w = e2 / p, i = e2 - w * p, e = b0 + w;
                     const int slot = e < LCAP ? lst_slot[e] : ov_slot[e];
@@ -639,12 +663,15 @@ alc_bulk32_kernel(B32Params P) {
                 // one warp per contender -> v_c, r_c and (fused) y_c - z^T u_c.
                 // The step's only contender is decided here, and its warp goes
                 // on to the winner's scalars.
+                #pragma unroll 1
                 for (int w = dw; w < ncon; w += DWARPS) {
                     dfl uu = df_zero(), uw = df_zero(), uz = df_zero();
                     float2 *uc = con_u + w * ldc;
+                    #pragma unroll 1
                     for (int t = lane; t < j; t += 32) {
                         const float2 *P0 = cpart + w * wpc * ldc + t;
                         dfl ut = ld2(P0);
+                        #pragma unroll 1
                         for (int q = 1; q < wpc; q++) ut = df_add_sloppy(ut, ld2(P0 + q * ldc));
                         ut = df_normalize(ut);
                         st2(uc + t, ut);
@@ -655,7 +682,7 @@ alc_bulk32_kernel(B32Params P) {
                     uu = df_normalize(uu);
                     uw = df_normalize(uw);
                     uz = df_normalize(uz);
-#pragma unroll
+#pragma unroll 1
                     for (int o = 16; o > 0; o >>= 1) {
                         const dfl ou{__shfl_xor_sync(LAGP_FULL_MASK, uu.hi, o), __shfl_xor_sync(LAGP_FULL_MASK, uu.lo, o)};
                         const dfl ow{__shfl_xor_sync(LAGP_FULL_MASK, uw.hi, o), __shfl_xor_sync(LAGP_FULL_MASK, uw.lo, o)};
@@ -764,7 +791,9 @@ alc_bulk32_kernel(B32Params P) {
                     // the new running best's vectors, before the next batch
                     // overwrites the batch arrays
                     const int wl = s_wl;
+                    #pragma unroll 1
                     for (int t = dt; t < j; t += DTHREADS) win_u[t] = con_u[wl * ldc + t];
+                    #pragma unroll 1
                     for (int i = dt; i < p; i += DTHREADS) win_x[i] = con_x[wl * p + i];
                     if (dt == 0) {
                         win_s[0] = con_v[wl];
@@ -812,14 +841,17 @@ alc_bulk32_kernel(B32Params P) {
                 const int t0 = dw * j / DWARPS, t1 = (dw + 1) * j / DWARPS;
                 float2 *part = cpart + dw * ldc;
                 df_tri_upper(wu, LT, ldl, t0, t1, lane, part);
+                #pragma unroll 1
                 for (int s = t1 + lane; s < j; s += 32) part[s] = make_float2(0.f, 0.f);
             }
+            #pragma unroll 1
             for (int i = dt; i < p; i += DTHREADS) xdd[i * ldx + j] = wx[i];
         }
         // (a double-float failure in the last step is seen here)
         __syncthreads();
         if (s_bad != LAGP_OK) status = s_bad;
         if (status != LAGP_OK) {
+            #pragma unroll 1
             for (int t = tid; t < nmax; t += THREADS) {
                 sel[t] = -1;
                 if (alc) alc[t] = CUDART_NAN;
