@@ -65,11 +65,13 @@
 // machine code (110 KB at CPT = 8 with the compiler's own unrolling) did not
 // fit: the set-up of a location and the double-float group's per-step phases
 // evicted one another.  The loops of the per-location set-up and outputs, of
-// the triangular products, of R3 and of the winner's bookkeeping therefore
-// carry `#pragma unroll 1` (85 KB); the Schur pass, the listing, R1, R2 and
-// the argmax of several contenders keep their unrolling, which the steps
-// with many contenders need.  Measured on the borehole batch: 11.4 -> 9.6 ms
-// a search, the same designs bit for bit.
+// the triangular products, of R3, of the argmax of several contenders and of
+// the winner's bookkeeping therefore carry `#pragma unroll 1`, and so does
+// the Schur pass's loop over the coordinates at CPT <= 8 (77 KB); the rest
+// of the Schur pass, the listing, R1 and R2 keep their unrolling, which the
+// wide candidate sets (CPT = 16) and the steps with many contenders need.
+// Measured on the borehole batch: 11.4 -> 9.4 ms a search, the same designs
+// bit for bit.
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -530,6 +532,7 @@ alc_bulk32_kernel(B32Params P) {
                         float s[CH];
 #pragma unroll
                         for (int r = 0; r < CH; r++) s[r] = 0.f;
+#pragma unroll(CPT <= 8 ? 1 : 4)
                         for (int ii = 0; ii < p; ii++) {
                             float cv[CH];
                             load_vec<CH>(Cg + ii * NPAD + c0 + h, cv);
@@ -745,7 +748,7 @@ alc_bulk32_kernel(B32Params P) {
                         }
                     }
                     int wl = lane;
-#pragma unroll
+#pragma unroll 1
                     for (int o = 16; o > 0; o >>= 1) {
                         const float oh = __shfl_xor_sync(LAGP_FULL_MASK, dl.hi, o);
                         const float ol = __shfl_xor_sync(LAGP_FULL_MASK, dl.lo, o);
