@@ -140,8 +140,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "701665b174e376f97131b52b0d9743d0d85b3c1f77606a6662757c4a4d62dd12",
-               "dram_bytes_per_location": (1.928700e9 + 0.788765e9) / 3040}
+ALC_TRAFFIC = {"sha256": "72c4d76973a6a7bb0196916473d8642202dfa2be23fc7d57906d1bb4e4630c64",
+               "dram_bytes_per_location": (1.781231e9 + 0.785989e9) / 3040}
 
 
 def alc_source_hash():
