@@ -104,7 +104,7 @@ typedef struct {
     int32_t ctas_per_sm;    /* resident CTAs per SM of the ALC kernels */
     int32_t block_threads;  /* threads per CTA of the ALC kernels */
     int32_t rescore_max;    /* F32BULK: contenders re-scored together in one
-                               batch, 1..32, used up to 8; 0 = automatic (the
+                               batch, 1..32, used up to 16; 0 = automatic (the
                                autotuner's choice for the shape, else 8).
                                More contenders take further batches, none is
                                dropped.  (F64SCHUR and F32BULK_F64: the
@@ -193,7 +193,7 @@ lagp_status lagp_df_check(lagp_ctx *ctx, const double *a, int64_t n, float *spli
  * a sample of the given problem (its first min(M, 16 x SMs) locations) for
  * every admissible number of resident CTAs per SM of the persistent kernel
  * and, for F32BULK with tuning.rescore_max == 0, for double-float re-score
- * batches of 8 and 4 contenders, and records the fastest for problems of
+ * batches of 16, 8 and 4 contenders, and records the fastest for problems of
  * this shape (precision, N' capacity, n_max, p, with or without prediction)
  * on this context; later calls with tuning.ctas_per_sm == 0 (and
  * rescore_max == 0) use it.  Results do not depend on either choice.

@@ -56,12 +56,12 @@ extern "C" lagp_status lagp_autotune(lagp_ctx *ctx, const void *X, int64_t N, in
     const int max_cps = (prec == LAGP_PREC_F32BULK || prec == LAGP_PREC_F32BULK_F64) ? 4 : 3;
     // the FP32-bulk kernel's re-score batch too (unless the user fixed it)
     const bool tune_b = prec == LAGP_PREC_F32BULK && ctx->tuning.rescore_max == 0;
-    const int batches[2] = {8, 4};
+    const int batches[3] = {16, 8, 4};
     float best_ms = 1e30f;
     int best = 0, best_b = 0;
     std::string key;
     lagp_status rc = LAGP_OK;
-    for (int trial = 0; trial < max_cps * (tune_b ? 2 : 1) && rc == LAGP_OK; trial++) {
+    for (int trial = 0; trial < max_cps * (tune_b ? 3 : 1) && rc == LAGP_OK; trial++) {
         const int cps = 1 + trial % max_cps, tb = tune_b ? batches[trial / max_cps] : 0;
         ctx->tune_override = cps;
         ctx->tune_tmax_override = tb;

@@ -144,13 +144,13 @@ def test_autotune_picks_a_grid_and_results_do_not_depend_on_it(L):
     idx, _ = L.lagp_knn(X, Xr, 600)
     before = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
     best = L.lagp_autotune(X, Xr, idx, 6, 25, w.d, w.g, prec="f32bulk", Y=Y)
-    assert 1 <= best["ctas_per_sm"] <= 4 and best["rescore_max"] in (4, 8)
+    assert 1 <= best["ctas_per_sm"] <= 4 and best["rescore_max"] in (4, 8, 16)
     after = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
     for k in ("sel", "mean", "s2", "alc"):
         assert torch.equal(torch.nan_to_num(before[k]), torch.nan_to_num(after[k])), k
     try:
         for cps in (1, 3):
-            for b in (1, 3, 8):
+            for b in (1, 3, 8, 16):
                 L.set_tuning(ctas_per_sm=cps, rescore_max=b)
                 out = L.lagp_alc_predict(X, Y, Xr, idx, 6, 25, w.d, w.g, want_alc=True)
                 for k in ("sel", "mean", "s2", "alc"):
