@@ -140,8 +140,8 @@ def fp64_flops(work, M, n, p, fused):
 # DRAM traffic (read + write) of the ALC kernel per location, from one ncu
 # capture of the kernel whose sources hash to `sha256` (the capture and its
 # command are summarised under profiles/); null for any other source.
-ALC_TRAFFIC = {"sha256": "72c4d76973a6a7bb0196916473d8642202dfa2be23fc7d57906d1bb4e4630c64",
-               "dram_bytes_per_location": (1.781231e9 + 0.785989e9) / 3040}
+ALC_TRAFFIC = {"sha256": "fd2b4ce9e01d018b093af71cbc1ff3268bbab5a2f0b259305f5276c41f82a647",
+               "dram_bytes_per_location": (1.804104e9 + 0.785168e9) / 3040}
 
 
 def alc_source_hash():
