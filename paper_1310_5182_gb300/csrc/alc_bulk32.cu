@@ -896,7 +896,10 @@ lagp_status launch_b32(lagp_ctx *ctx, const AlcArgs &a) {
     constexpr int NPAD = FTHREADS * CPT;
     cudaStream_t st = ctx->stream;
     const std::string key = alc_shape_key("alc_f32", CPT, a.nmax, a.p, a.mean != nullptr);
-    const int tmax = std::max(1, std::min(alc_rescore_batch(ctx, key), TMAX_CAP));
+    int tmax = std::max(1, std::min(alc_rescore_batch(ctx, key), TMAX_CAP));
+    // the largest batch whose vectors fit in shared memory (the batch size
+    // changes no result)
+    while (tmax > 1 && b32_smem_bytes(a.nmax, a.p, tmax, NPAD) > ctx->smem_optin) tmax--;
     auto kern = alc_bulk32_kernel<CPT>;
     const size_t smem = b32_smem_bytes(a.nmax, a.p, tmax, NPAD);
     if (smem > ctx->smem_optin)
