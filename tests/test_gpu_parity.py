@@ -332,6 +332,36 @@ def test_select_ragged_uneven(L, O, prec):
     _select_case(L, O, w, prec, Np_arr=Np_arr, n_arr=n_arr, max_diverged=0.05)
 
 
+def test_select_batch_clamped_to_shared_memory(L, O):
+    """p = 20, n = 128, N' = 2048: at re-score batches of 16 the double-float
+    vectors would not fit in shared memory beside L^{-1} and the 20-d design
+    coordinates, and the launcher takes the largest batch that fits.  An
+    explicit request for 16 and the tuner's trials both succeed, with the
+    designs, ALC values and predictions of batches of 4 bit for bit (the batch
+    size changes no result)."""
+    rng = np.random.default_rng(58)
+    X = rng.uniform(0.0, 1.0, (12_000, 20))
+    Y = np.sin(X.sum(1)) + 0.1 * X[:, 0] ** 2
+    Xr = rng.uniform(0.2, 0.8, (4, 20))
+    Xd, Yd, Xrd = dev(X), dev(Y), dev(Xr)
+    idx, _ = L.lagp_knn(Xd, Xrd, 2048)
+    args = (Xd, Yd, Xrd, idx, 6, 128, 20.0, 1e-3)
+    try:
+        L.set_tuning(rescore_max=4)
+        ref = L.lagp_alc_predict(*args, want_alc=True)
+        L.set_tuning(rescore_max=16)
+        big = L.lagp_alc_predict(*args, want_alc=True)
+        L.set_tuning(rescore_max=0)
+        L.lagp_autotune(Xd, Xrd, idx, 6, 128, 20.0, 1e-3, prec="f32bulk", Y=Yd)
+        tuned = L.lagp_alc_predict(*args, want_alc=True)
+    finally:
+        L.set_tuning(rescore_max=0)
+    assert (ref["status"].cpu().numpy() == 0).all()
+    for out in (big, tuned):
+        for k in ("status", "sel", "alc", "mean", "s2"):
+            assert torch.equal(torch.nan_to_num(ref[k]), torch.nan_to_num(out[k])), k
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32bulk", "f32bulk_f64", "f64schur"])
 def test_select_slab3d(L, O, prec):
     w = W.slab3d(seed=8, N=30_000, grid=(4, 4, 3), n=30, Np=300)
