@@ -517,7 +517,10 @@ def other_configs(L, dev, args, flush):
     call (its wall time, copies included)."""
     out = {}
     w1 = W.c1_toy2d_fp64()
-    for prec in ("f64", "f32bulk"):
+    # the plain FP64 form (the paper's O(j^2) criterion), the FP64 Schur form
+    # (the incremental O(j) criterion, exact to FP64 rounding) and the
+    # FP32-bulk form
+    for prec in ("f64", "f64schur", "f32bulk"):
         out[f"toy2d_N10000_M100_n50_Nprime1000_{prec}"] = config_leg(L, dev, w1, prec, 10, 3, flush, oracle_S=100)
     legs = [("borehole8d_N1000000_M20000_n30-100_Nprime500-2000_mle", W.c3_borehole_1m_uneven, 2, 1),
             ("slab3d_N500000_grid60x60x56_n60_Nprime1500_mle", W.c4_slab3d, 1, 1),
