@@ -511,7 +511,7 @@ def alc_eval_sweep(L, dev, flush, ns=range(16, 513, 4), Nc=60_000, oracle_ns=(16
 
 
 def other_configs(L, dev, args, flush):
-    """BASELINE's other configurations on this GPU, each against the FP64
+    """The other workload configurations on this GPU, each against the FP64
     oracle on a seeded subsample (the 2-d toy: all 100 locations; the others:
     1,000), and the 4M-point borehole also end to end through the host-buffer
     call (its wall time, copies included)."""
